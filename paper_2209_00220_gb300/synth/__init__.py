@@ -1,0 +1,217 @@
+"""Seeded synthetic inputs for ByteStore workloads (shared by the oracle's tests,
+the GPU parity tests and ``bench.py``).
+
+This module only draws random numbers and maps them to plain int32 column
+values and predicate literals. It contains none of the storage method's
+arithmetic: no dictionary, no prefix-preserving code, no layout and no scan.
+
+Workload recipes (Section 6.1 of the paper generates a column of 10^9 values in
+[0, 2^d) drawn from a Zipf distribution; the paper does not say which value gets
+which Zipf rank, so a seeded bijection decides it):
+
+* ``zipf_column(n, N, s, seed, mapping)``: rank r ~ Zipf(s) over N ranks
+  (s = 0 is uniform), value = mapping(r).
+* ``config_single_column``: 2^20 rows, Zipf s = 1.0 over a seeded set of 65,536
+  distinct signed int32 values (seeded shuffle decides which value is frequent).
+* ``config_sweep_column``: values in [0, 2^d) (d = 32: the whole int32 range) via
+  a seeded Feistel bijection of the rank, or the identity ("monotone").
+* ``pick_literals``: literals that reach a target selectivity on a bounded
+  seeded sample of the column (the achieved selectivity is always measured on
+  the result, never assumed).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "synth.c")
+_LIB_PATH = os.path.join(_HERE, "libbssynth.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile ``synth.c`` into ``libbssynth.so`` beside it (gcc, -O2)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-pthread",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            u64, i32, dbl, vp = ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+            lib.synth_u64.argtypes = [u64, u64, u64, u64, vp, i32]
+            lib.synth_u64.restype = None
+            lib.synth_zipf.argtypes = [u64, u64, u64, u64, dbl, vp, i32]
+            lib.synth_zipf.restype = i32
+            lib.synth_feistel.argtypes = [vp, u64, i32, u64, vp, i32]
+            lib.synth_feistel.restype = i32
+            lib.synth_gather.argtypes = [vp, u64, vp, vp, i32]
+            lib.synth_gather.restype = None
+            _lib = lib
+    return _lib
+
+
+def _threads() -> int:
+    try:
+        return max(1, min(64, len(os.sched_getaffinity(0))))
+    except AttributeError:  # pragma: no cover
+        return max(1, min(64, os.cpu_count() or 1))
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+# ----------------------------------------------------------------- primitives
+def u64(seed: int, stream: int, n: int, start: int = 0) -> np.ndarray:
+    """n counter-based 64-bit draws of (seed, stream), indices start..start+n-1."""
+    out = np.empty(n, dtype=np.uint64)
+    _load().synth_u64(seed, stream, start, n, _ptr(out), _threads())
+    return out
+
+
+def zipf_ranks(n: int, N: int, s: float, seed: int, stream: int = 0) -> np.ndarray:
+    """n ranks in [0, N) with P(rank r) proportional to (r + 1)^-s."""
+    out = np.empty(n, dtype=np.uint32)
+    rc = _load().synth_zipf(seed, stream, n, N, float(s), _ptr(out), _threads())
+    if rc != 0:
+        raise ValueError("synth_zipf failed (%d) for N=%d s=%g" % (rc, N, s))
+    return out
+
+
+def feistel(x: np.ndarray, d: int, seed: int) -> np.ndarray:
+    """Seeded bijection of [0, 2^d) applied to every element of x (uint32)."""
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    out = np.empty_like(x)
+    rc = _load().synth_feistel(_ptr(x), x.size, d, seed, _ptr(out), _threads())
+    if rc != 0:
+        raise ValueError("bad d=%d" % d)
+    return out
+
+
+def gather(idx: np.ndarray, table: np.ndarray) -> np.ndarray:
+    idx = np.ascontiguousarray(idx, dtype=np.uint32)
+    table = np.ascontiguousarray(table, dtype=np.int32)
+    if idx.size and int(idx.max()) >= table.size:
+        raise IndexError("gather index out of range")
+    out = np.empty(idx.size, dtype=np.int32)
+    _load().synth_gather(_ptr(idx), idx.size, _ptr(table), _ptr(out), _threads())
+    return out
+
+
+def distinct_values(count: int, seed: int, stream: int = 7) -> np.ndarray:
+    """A seeded set of ``count`` distinct signed int32 values, sorted ascending."""
+    have = np.empty(0, dtype=np.int32)
+    start = 0
+    while have.size < count:
+        need = (count - have.size) * 2 + 64
+        cand = u64(seed, stream, need, start).astype(np.uint32).view(np.int32)
+        start += need
+        allv = np.concatenate([have, cand])
+        _, first = np.unique(allv, return_index=True)
+        have = allv[np.sort(first)][:count]
+    return np.sort(have)
+
+
+def permutation(count: int, seed: int, stream: int = 11) -> np.ndarray:
+    """Seeded permutation of range(count) (argsort of counter-based keys)."""
+    keys = u64(seed, stream, count)
+    return np.argsort(keys, kind="stable")
+
+
+# -------------------------------------------------------------------- columns
+def zipf_column(n: int, N: int, s: float, seed: int, mapping="feistel", d: int | None = None,
+                stream: int = 0) -> np.ndarray:
+    """n int32 values: rank ~ Zipf(s) over N ranks, value = mapping(rank).
+
+    mapping: "identity" (value = rank, the monotone variant), "feistel" (seeded
+    bijection of [0, 2^d), N must be 2^d), or an int32 table of N values.
+    """
+    r = zipf_ranks(n, N, s, seed, stream)
+    if isinstance(mapping, str):
+        if mapping == "identity":
+            return r.view(np.int32) if N > (1 << 31) else r.astype(np.int32)
+        if mapping == "feistel":
+            if d is None or N != (1 << d):
+                raise ValueError("feistel mapping needs N == 2^d")
+            return feistel(r, d, seed ^ 0x5A5A).view(np.int32)
+        raise ValueError(mapping)
+    return gather(r, np.asarray(mapping, dtype=np.int32))
+
+
+def config_single_column(seed: int = 0, n: int = 1 << 20, distinct: int = 65536, s: float = 1.0):
+    """Zipf(s) over a seeded set of ``distinct`` signed int32 values.
+
+    Returns (values, domain) where domain is the sorted value set (the declared
+    dictionary of the fixed-width layouts)."""
+    domain = distinct_values(distinct, seed)
+    table = domain[permutation(distinct, seed)]
+    return zipf_column(n, distinct, s, seed, mapping=table), domain
+
+
+def config_sweep_column(n: int, d: int, s: float, seed: int, monotone: bool = False) -> np.ndarray:
+    """Values in [0, 2^d) for d < 32 (whole int32 range for d = 32), rank ~ Zipf(s)."""
+    N = 1 << d
+    r = zipf_ranks(n, N, s, seed)
+    if not monotone:
+        r = feistel(r, d, seed ^ 0x5A5A)
+    return r.view(np.int32)
+
+
+def domain_min_for_bits(d: int) -> int:
+    return -(1 << 31) if d == 32 else 0
+
+
+# ------------------------------------------------------------------- literals
+OPS = ("lt", "le", "gt", "ge", "eq", "ne", "between")
+
+
+def _sample(values: np.ndarray, seed: int, k: int = 1 << 20) -> np.ndarray:
+    if values.size <= k:
+        return np.sort(values.astype(np.int64))
+    idx = (u64(seed, 99, k) % np.uint64(values.size)).astype(np.int64)
+    return np.sort(values[idx].astype(np.int64))
+
+
+def pick_literals(values: np.ndarray, op: str, target: float, seed: int = 0):
+    """Literals (lit, lit2) aiming at selectivity ``target`` for ``op``.
+
+    lt/le/gt/ge: a sample quantile. eq/ne: the sampled value whose frequency is
+    closest to target (eq) or 1 - target (ne). between: [q0, q0 + target]
+    quantiles with q0 seeded. Values are plain int32; lit2 is 0 unless between.
+    """
+    smp = _sample(values, seed)
+    m = smp.size
+    int32 = lambda x: int(np.clip(x, -(1 << 31), (1 << 31) - 1))
+    if op in ("lt", "ge"):
+        q = target if op == "lt" else 1.0 - target
+        c = smp[min(m - 1, int(q * m))]
+        return int32(c), 0
+    if op in ("le", "gt"):
+        q = target if op == "le" else 1.0 - target
+        i = int(q * m) - 1
+        return (int32(smp[0] - 1) if i < 0 else int32(smp[min(m - 1, i)])), 0
+    if op in ("eq", "ne"):
+        u, cnt = np.unique(smp, return_counts=True)
+        f = cnt / m
+        want = target if op == "eq" else 1.0 - target
+        return int32(u[int(np.argmin(np.abs(f - want)))]), 0
+    if op == "between":
+        q0 = float(u64(seed, 123, 1)[0] >> np.uint64(11)) / float(1 << 53) * max(0.0, 1.0 - target)
+        lo = smp[min(m - 1, int(q0 * m))]
+        hi = smp[min(m - 1, max(0, int((q0 + target) * m) - 1))]
+        return int32(lo), int32(max(lo, hi))
+    raise ValueError(op)
