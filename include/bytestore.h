@@ -1,0 +1,232 @@
+/*
+ * bytestore.h -- C ABI of the GB300 ByteStore library (libbytestore.so).
+ *
+ * ByteStore (Zhang, Feng, Lo, Qin, "ByteStore: Hybrid Layouts for Main-Memory
+ * Column Stores") stores each int32 column in one of three layouts and runs two
+ * operations on it:
+ *   - scan:   column + predicate -> result bit vector       (Section 2.2, Alg. 3)
+ *   - lookup: column + result bit vector -> int32 values     (Section 2.2, Alg. 4)
+ * Layouts: PP-VBS (prefix-preserving encoding, Algorithm 1, stored as Variable
+ * Byte Slice, Section 3.2), ByteSlice (Section 2.5) and Bit-Packed (Section 2.3).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: BS_OK (0) or a negative BS_ERR_* status. Nothing aborts.
+ *   - Pointers named d_* are device pointers (CUDA global memory on the
+ *     column's device); h_* are host pointers. The caller owns every buffer it
+ *     passes; a bs_column owns its own device and host buffers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Scans and lookups are asynchronous and stream-ordered; a device-
+ *     side consistency failure is recorded in a device status word and reported
+ *     by bs_last_device_error() after the stream has been synchronised.
+ *   - Result bit vectors are arrays of uint32 words: bit i of word w is row
+ *     32*w + i (Section 3.3.1 builds R from 32-bit movemask words). A scan
+ *     writes ceil(n/32) words and leaves every bit at or past n zero; input bit
+ *     vectors may hold anything at or past n (it is ignored).
+ *   - Literals are plain int32 values; the library encodes them with the
+ *     column's dictionary (Section 2.2). Literals absent from the dictionary are
+ *     rewritten to an equivalent predicate on present values.
+ *   - Row ids are uint32 (a column has fewer than 2^32 rows).
+ */
+#ifndef BYTESTORE_H
+#define BYTESTORE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define BS_OK 0
+#define BS_ERR_INVALID_ARG (-1)   /* bad pointer, size, op or layout */
+#define BS_ERR_OOM (-2)           /* host or device allocation failed */
+#define BS_ERR_CUDA (-3)          /* a CUDA runtime call failed */
+#define BS_ERR_CAPACITY (-4)      /* output buffer smaller than the result */
+#define BS_ERR_UNSUPPORTED (-5)   /* valid request this column cannot serve */
+#define BS_ERR_TIMEOUT (-6)       /* a bounded device or host wait expired */
+#define BS_ERR_DEVICE_CHECK (-7)  /* a kernel's bounds check fired */
+#define BS_ERR_NOT_READY (-8)     /* asynchronous result not complete yet */
+
+typedef enum { BS_BITPACKED = 0, BS_BYTESLICE = 1, BS_PPVBS = 2 } bs_layout;
+
+/* Predicate types of Section 2.2; BETWEEN is inclusive on both ends. */
+typedef enum { BS_LT = 0, BS_LE = 1, BS_GT = 2, BS_GE = 3, BS_EQ = 4, BS_NE = 5, BS_BETWEEN = 6 } bs_op;
+
+typedef struct bs_column bs_column; /* opaque; owns its device buffers */
+
+/* Encoding options (NULL selects all defaults).
+ *   domain_bits / domain_min: for BS_BYTESLICE and BS_BITPACKED, declare the
+ *       code of value v to be v - domain_min over [0, 2^domain_bits)
+ *       (1 <= domain_bits <= 32). 0 = use a dictionary instead.
+ *   domain_values / n_domain: for BS_BYTESLICE and BS_BITPACKED, a declared
+ *       dictionary (distinct int32 values in any order); code = rank of the
+ *       value in it. NULL = the column's observed distinct values. PP-VBS always
+ *       encodes the observed values with their frequencies (Algorithm 1).
+ *   device: CUDA device ordinal, -1 = the current device.
+ *   host_only: 1 = build the layout in host memory only (no GPU needed); such a
+ *       column answers bs_column_row_codes / bs_column_get_info but not scans.
+ *   keep_host: 1 = keep the host copy of the layout after the upload.
+ *   threads: host encoder threads, 0 = every available core. */
+typedef struct {
+    int32_t domain_bits;
+    int32_t device;
+    int64_t domain_min;
+    const int32_t *domain_values;
+    uint64_t n_domain;
+    int32_t host_only;
+    int32_t keep_host;
+    int32_t threads;
+    int32_t reserved;
+} bs_encode_opts;
+
+/* ------------------------------------------------------------- columns */
+
+/* Encode n int32 values (host memory, read only during the call) into `layout`
+ * and upload the layout to the device (Section 2.2 dictionary encoding; PP-VBS
+ * codes by Algorithm 1 and stored as VBS, Section 3.2; ByteSlice by Section 2.5;
+ * Bit-Packed by Section 2.3). On success *out owns a new column; free it with
+ * bs_column_free. n may be 0. Errors: INVALID_ARG (NULL pointers, n >= 2^32,
+ * value outside a declared domain), OOM, CUDA. */
+int bs_encode_column(const int32_t *h_values, uint64_t n, bs_layout layout,
+                     const bs_encode_opts *opts, bs_column **out);
+
+/* Test hook: build a column straight from codes, without a dictionary.
+ * PP-VBS: h_codes[i] is an unpadded code of h_lens[i] bytes (1..8; first byte
+ * most significant) -- any code set whose every extension of a shorter code has
+ * a positive tail (the premise of Lemma 1). ByteSlice / Bit-Packed: h_codes[i]
+ * < 2^code_bits, h_lens ignored (may be NULL). Such a column is scanned with
+ * bs_scan_code and read back with bs_lookup_codes. */
+int bs_column_from_codes(const uint64_t *h_codes, const uint8_t *h_lens, uint64_t n, bs_layout layout,
+                         int32_t code_bits, const bs_encode_opts *opts, bs_column **out);
+
+void bs_column_free(bs_column *col);
+
+typedef struct {
+    uint64_t n_rows;
+    int32_t layout;          /* bs_layout */
+    int32_t max_code_bytes;  /* PP-VBS: K (longest code); ByteSlice: number of slices */
+    int32_t code_bits;       /* ByteSlice / Bit-Packed: k */
+    int32_t on_device;
+    uint64_t n_dict;         /* dictionary entries (0 for a declared range or raw codes) */
+    uint64_t device_bytes;   /* HBM held by the column (layout + GPU index + decode tables) */
+    uint64_t layout_bytes;   /* bytes of the paper's layout alone (Section 6.1.4 counts masks) */
+    uint64_t len_hist[9];    /* PP-VBS: rows whose code has 1..8 bytes at [1..8] */
+} bs_column_info;
+
+int bs_column_get_info(const bs_column *col, bs_column_info *info);
+
+/* Per-row codes (unpadded, first byte most significant) and lengths in bytes for
+ * rows [row_begin, row_begin + count), read from the host copy of the layout.
+ * ByteSlice / Bit-Packed report the k-bit code and length ceil(k/8).
+ * Errors: INVALID_ARG (range), UNSUPPORTED (no host copy kept). */
+int bs_column_row_codes(const bs_column *col, uint64_t row_begin, uint64_t count,
+                        uint64_t *h_codes, uint8_t *h_lens);
+
+/* The dictionary: sorted distinct values with their codes and code lengths
+ * (PP-VBS: Algorithm 1's C and L; ByteSlice / Bit-Packed: the rank and ceil(k/8)).
+ * Writes min(cap, n_dict) entries; any output may be NULL. */
+int bs_column_dictionary(const bs_column *col, int32_t *h_values, uint64_t *h_codes, uint8_t *h_lens,
+                         uint64_t cap);
+
+/* --------------------------------------------------------------- scan */
+
+/* Scan (Section 2.2; PP-VBS by Algorithm 3 and Lemma 1; ByteSlice and
+ * Bit-Packed by Sections 2.5 and 2.3): bit i of d_bits = (v_i op lit), or
+ * lit <= v_i <= lit2 for BS_BETWEEN (lit2 ignored otherwise). d_bits: device,
+ * ceil(n/32) words, fully written. Errors: INVALID_ARG, UNSUPPORTED (raw-code
+ * column or host-only column), CUDA. */
+int bs_scan(const bs_column *col, bs_op op, int32_t lit, int32_t lit2, uint32_t *d_bits, void *stream);
+
+/* Seeded scan, the bit-vector pipelining of Section 3.3.1: d_bits = d_seed AND
+ * scan(op, lit, lit2). Rows whose seed bit is 0 are never examined, so blocks
+ * with an all-zero seed word stop before reading any byte slice. d_seed may
+ * equal d_bits (in place). */
+int bs_scan_seeded(const bs_column *col, bs_op op, int32_t lit, int32_t lit2, const uint32_t *d_seed,
+                   uint32_t *d_bits, void *stream);
+
+/* Scan with literal codes instead of values (raw-code columns and tests).
+ * PP-VBS: code/len is an unpadded code of len bytes (1..8) compared with every
+ * row's code as if both were zero-padded (Section 3.1.1). ByteSlice /
+ * Bit-Packed: code is a k-bit code, len ignored. code2/len2: upper literal of
+ * BS_BETWEEN. */
+int bs_scan_code(const bs_column *col, bs_op op, uint64_t code, int32_t len, uint64_t code2, int32_t len2,
+                 const uint32_t *d_seed, uint32_t *d_bits, void *stream);
+
+/* One predicate of a conjunction. */
+typedef struct {
+    const bs_column *col;
+    int32_t op;   /* bs_op */
+    int32_t lit;
+    int32_t lit2;
+    int32_t reserved;
+} bs_pred;
+
+/* Conjunction of npreds (1..16) predicates over columns of equal length, each
+ * scan seeded with the running result (Section 3.3.1, pipelined bit vectors).
+ * d_bits: ceil(n/32) words. */
+int bs_scan_conj(const bs_pred *preds, int32_t npreds, uint32_t *d_bits, void *stream);
+
+/* ------------------------------------------------------------- lookup */
+
+/* Device workspace bytes bs_lookup / bs_lookup_codes need for this column. */
+uint64_t bs_lookup_workspace_bytes(const bs_column *col);
+
+/* Lookup (Section 2.2, Algorithm 4): for every set bit i < n of d_bits, in
+ * ascending row order, write v_i to d_out (device int32, out_cap entries).
+ * The number of set bits is written to *d_count (device uint64, may be NULL)
+ * even when it exceeds out_cap; only the first out_cap values are written.
+ * d_workspace: device scratch of bs_lookup_workspace_bytes(col) bytes, or NULL
+ * to let the call allocate (stream-ordered) and free it. */
+int bs_lookup(const bs_column *col, const uint32_t *d_bits, int32_t *d_out, uint64_t out_cap,
+              uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes, void *stream);
+
+/* Same as bs_lookup but returns the zero-padded codes Algorithm 4 builds
+ * (PP-VBS: K bytes; ByteSlice / Bit-Packed: the k-bit code) as uint64. */
+int bs_lookup_codes(const bs_column *col, const uint32_t *d_bits, uint64_t *d_codes, uint64_t out_cap,
+                    uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes, void *stream);
+
+/* Lookup by row ids in caller order: d_out[t] = v_{d_rowids[t]}, t < m.
+ * Row ids >= n set the device status word (BS_ERR_DEVICE_CHECK) and write 0. */
+int bs_lookup_rowids(const bs_column *col, const uint32_t *d_rowids, uint64_t m, int32_t *d_out,
+                     void *stream);
+
+/* ---------------------------------------------------- layout advisor */
+
+#define BS_ADVISE_TIMED 0        /* Algorithm 5: time 100 scans per layout on the GPU */
+#define BS_ADVISE_BYTES_MODEL 1  /* deterministic: bytes the scans must read, no timing */
+
+typedef struct {
+    int32_t layout;          /* chosen bs_layout (BS_BYTESLICE or BS_PPVBS) */
+    int32_t n_points;        /* literals profiled (100) */
+    double auc_byteslice;    /* area under the (selectivity, cost) curve */
+    double auc_ppvbs;
+    double selectivity[100];
+    double cost_byteslice[100];  /* seconds (TIMED) or bytes (BYTES_MODEL) */
+    double cost_ppvbs[100];
+} bs_advice;
+
+/* Column-layout advisor (Algorithm 5) for one numerical column: encode it as
+ * ByteSlice and as PP-VBS, profile `<` scans with 100 literals spread over the
+ * selectivity range, integrate each profile by the trapezoid rule and keep the
+ * smaller area (ties -> ByteSlice). opts as for bs_encode_column. */
+int bs_advise_layout(const int32_t *h_values, uint64_t n, int32_t mode, const bs_encode_opts *opts,
+                     bs_advice *out);
+
+/* -------------------------------------------------------- diagnostics */
+
+const char *bs_strerror(int status);
+
+/* Reads and clears the device status word of the current device (a kernel
+ * bounds check or a bounded wait that gave up). Synchronises the device.
+ * Returns BS_OK, BS_ERR_DEVICE_CHECK or BS_ERR_TIMEOUT. */
+int bs_last_device_error(void);
+
+/* Library version string. */
+const char *bs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BYTESTORE_H */

@@ -1,0 +1,330 @@
+"""ctypes binding of libbytestore with the C ABI's names (include/bytestore.h).
+
+Argument marshalling only: every step of a scan or lookup runs in the CUDA
+library. Device buffers are torch CUDA tensors (result bit vectors are int32
+tensors holding uint32 words); streams default to torch's current stream.
+The library is loaded on first use; if it is missing this module raises
+ImportError -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbytestore.so")
+
+LAYOUTS = {"bitpacked": 0, "byteslice": 1, "ppvbs": 2}
+OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6}
+ADVISE_TIMED, ADVISE_BYTES_MODEL = 0, 1
+
+BS_OK, BS_ERR_INVALID_ARG, BS_ERR_OOM, BS_ERR_CUDA = 0, -1, -2, -3
+BS_ERR_CAPACITY, BS_ERR_UNSUPPORTED, BS_ERR_TIMEOUT, BS_ERR_DEVICE_CHECK, BS_ERR_NOT_READY = -4, -5, -6, -7, -8
+
+_u64, _i32, _i64, _vp = ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+
+
+class bs_encode_opts(ctypes.Structure):
+    _fields_ = [("domain_bits", _i32), ("device", _i32), ("domain_min", _i64), ("domain_values", _vp),
+                ("n_domain", _u64), ("host_only", _i32), ("keep_host", _i32), ("threads", _i32),
+                ("reserved", _i32)]
+
+
+class bs_column_info(ctypes.Structure):
+    _fields_ = [("n_rows", _u64), ("layout", _i32), ("max_code_bytes", _i32), ("code_bits", _i32),
+                ("on_device", _i32), ("n_dict", _u64), ("device_bytes", _u64), ("layout_bytes", _u64),
+                ("len_hist", _u64 * 9)]
+
+
+class bs_pred(ctypes.Structure):
+    _fields_ = [("col", _vp), ("op", _i32), ("lit", _i32), ("lit2", _i32), ("reserved", _i32)]
+
+
+class bs_advice(ctypes.Structure):
+    _fields_ = [("layout", _i32), ("n_points", _i32), ("auc_byteslice", ctypes.c_double),
+                ("auc_ppvbs", ctypes.c_double), ("selectivity", ctypes.c_double * 100),
+                ("cost_byteslice", ctypes.c_double * 100), ("cost_ppvbs", ctypes.c_double * 100)]
+
+
+_SIGS = {
+    "bs_encode_column": ([_vp, _u64, _i32, _vp, _vp], _i32),
+    "bs_column_from_codes": ([_vp, _vp, _u64, _i32, _i32, _vp, _vp], _i32),
+    "bs_column_free": ([_vp], None),
+    "bs_column_get_info": ([_vp, _vp], _i32),
+    "bs_column_row_codes": ([_vp, _u64, _u64, _vp, _vp], _i32),
+    "bs_column_dictionary": ([_vp, _vp, _vp, _vp, _u64], _i32),
+    "bs_scan": ([_vp, _i32, _i32, _i32, _vp, _vp], _i32),
+    "bs_scan_seeded": ([_vp, _i32, _i32, _i32, _vp, _vp, _vp], _i32),
+    "bs_scan_code": ([_vp, _i32, _u64, _i32, _u64, _i32, _vp, _vp, _vp], _i32),
+    "bs_scan_conj": ([_vp, _i32, _vp, _vp], _i32),
+    "bs_lookup_workspace_bytes": ([_vp], _u64),
+    "bs_lookup": ([_vp, _vp, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
+    "bs_lookup_codes": ([_vp, _vp, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
+    "bs_lookup_rowids": ([_vp, _vp, _u64, _vp, _vp], _i32),
+    "bs_advise_layout": ([_vp, _u64, _i32, _vp, _vp], _i32),
+    "bs_strerror": ([_i32], ctypes.c_char_p),
+    "bs_last_device_error": ([], _i32),
+    "bs_version": ([], ctypes.c_char_p),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build_library(force: bool = False) -> str:
+    from . import build_lib
+    return build_lib.build(force=force)
+
+
+def lib():
+    """The loaded libbytestore (ImportError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError("libbytestore.so is not built (%s); run "
+                                  "`python -m paper_2209_00220_gb300.build_lib`" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+class BsError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = lib().bs_strerror(status).decode()
+        super().__init__("%s: %s (%d)" % (what, msg, status) if what else "%s (%d)" % (msg, status))
+
+
+def _check(rc: int, what: str):
+    if rc != BS_OK:
+        raise BsError(rc, what)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _opts(domain_bits=0, domain_min=0, domain_values=None, device=-1, host_only=False, keep_host=False,
+          threads=0):
+    o = bs_encode_opts()
+    o.domain_bits = int(domain_bits)
+    o.domain_min = int(domain_min)
+    o.device = int(device)
+    o.host_only = 1 if host_only else 0
+    o.keep_host = 1 if keep_host else 0
+    o.threads = int(threads)
+    keep = None
+    if domain_values is not None:
+        keep = _np(domain_values, np.int32)
+        o.domain_values = keep.ctypes.data
+        o.n_domain = keep.size
+    return o, keep
+
+
+class Column:
+    """Owns one bs_column (freed with the object)."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = handle
+        self.n = n
+
+    @property
+    def n_words(self) -> int:
+        return (self.n + 31) // 32
+
+    def info(self) -> dict:
+        return bs_column_get_info(self)
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.bs_column_free(h)
+
+    def free(self):
+        self.__del__()
+
+
+# ----------------------------------------------------------------- columns
+def bs_encode_column(values, layout: str = "ppvbs", **opts) -> Column:
+    v = _np(values, np.int32)
+    o, keep = _opts(**opts)
+    out = _vp()
+    _check(lib().bs_encode_column(v.ctypes.data if v.size else None, v.size, LAYOUTS[layout],
+                                  ctypes.byref(o), ctypes.byref(out)), "bs_encode_column")
+    del keep
+    return Column(out.value, v.size)
+
+
+def bs_column_from_codes(codes, lens, layout: str = "ppvbs", code_bits: int = 0, **opts) -> Column:
+    c = _np(codes, np.uint64)
+    ln = _np(lens, np.uint8) if lens is not None else None
+    o, keep = _opts(**opts)
+    out = _vp()
+    _check(lib().bs_column_from_codes(c.ctypes.data if c.size else None,
+                                      ln.ctypes.data if ln is not None and ln.size else None, c.size,
+                                      LAYOUTS[layout], int(code_bits), ctypes.byref(o), ctypes.byref(out)),
+           "bs_column_from_codes")
+    return Column(out.value, c.size)
+
+
+def bs_column_free(col: Column):
+    col.free()
+
+
+def bs_column_get_info(col: Column) -> dict:
+    i = bs_column_info()
+    _check(lib().bs_column_get_info(col.handle, ctypes.byref(i)), "bs_column_get_info")
+    return {"n_rows": i.n_rows, "layout": i.layout, "max_code_bytes": i.max_code_bytes,
+            "code_bits": i.code_bits, "on_device": bool(i.on_device), "n_dict": i.n_dict,
+            "device_bytes": i.device_bytes, "layout_bytes": i.layout_bytes, "len_hist": list(i.len_hist)}
+
+
+def bs_column_row_codes(col: Column, begin: int = 0, count: int | None = None):
+    count = col.n - begin if count is None else count
+    codes = np.zeros(max(1, count), np.uint64)
+    lens = np.zeros(max(1, count), np.uint8)
+    _check(lib().bs_column_row_codes(col.handle, begin, count, codes.ctypes.data, lens.ctypes.data),
+           "bs_column_row_codes")
+    return codes[:count], lens[:count]
+
+
+def bs_column_dictionary(col: Column):
+    nd = col.info()["n_dict"]
+    v = np.zeros(max(1, nd), np.int32)
+    c = np.zeros(max(1, nd), np.uint64)
+    ln = np.zeros(max(1, nd), np.uint8)
+    _check(lib().bs_column_dictionary(col.handle, v.ctypes.data, c.ctypes.data, ln.ctypes.data, nd),
+           "bs_column_dictionary")
+    return v[:nd], c[:nd], ln[:nd]
+
+
+# -------------------------------------------------------------------- scan
+def _bits_out(col: Column, out):
+    if out is None:
+        import torch
+        out = torch.empty(max(1, col.n_words), dtype=torch.int32, device="cuda")
+    return out
+
+
+def bs_scan(col: Column, op: str, lit: int, lit2: int = 0, out=None, stream=None):
+    out = _bits_out(col, out)
+    _check(lib().bs_scan(col.handle, OPS[op], int(lit), int(lit2), _dptr(out), _stream(stream)), "bs_scan")
+    return out
+
+
+def bs_scan_seeded(col: Column, op: str, lit: int, lit2: int, seed, out=None, stream=None):
+    out = _bits_out(col, out)
+    _check(lib().bs_scan_seeded(col.handle, OPS[op], int(lit), int(lit2), _dptr(seed), _dptr(out),
+                                _stream(stream)), "bs_scan_seeded")
+    return out
+
+
+def bs_scan_code(col: Column, op: str, code: int, length: int = 0, code2: int = 0, length2: int = 0,
+                 seed=None, out=None, stream=None):
+    out = _bits_out(col, out)
+    _check(lib().bs_scan_code(col.handle, OPS[op], int(code), int(length), int(code2), int(length2),
+                              _dptr(seed), _dptr(out), _stream(stream)), "bs_scan_code")
+    return out
+
+
+def bs_scan_conj(preds, out=None, stream=None):
+    """preds: sequence of (Column, op, lit[, lit2])."""
+    arr = (bs_pred * len(preds))()
+    for i, p in enumerate(preds):
+        arr[i].col = p[0].handle
+        arr[i].op = OPS[p[1]]
+        arr[i].lit = int(p[2])
+        arr[i].lit2 = int(p[3]) if len(p) > 3 else 0
+    out = _bits_out(preds[0][0], out)
+    _check(lib().bs_scan_conj(arr, len(preds), _dptr(out), _stream(stream)), "bs_scan_conj")
+    return out
+
+
+# ------------------------------------------------------------------ lookup
+def bs_lookup_workspace_bytes(col: Column) -> int:
+    return int(lib().bs_lookup_workspace_bytes(col.handle))
+
+
+def bs_lookup(col: Column, bits, out=None, out_cap: int | None = None, count=None, workspace=None,
+              stream=None):
+    """Returns (values tensor, count tensor (int64, 1 element on the device))."""
+    import torch
+    if out is None:
+        out = torch.empty(max(1, col.n if out_cap is None else out_cap), dtype=torch.int32, device="cuda")
+    cap = out.numel() if out_cap is None else int(out_cap)
+    if count is None:
+        count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(lib().bs_lookup(col.handle, _dptr(bits), _dptr(out), cap, _dptr(count), _dptr(workspace), ws_bytes,
+                           _stream(stream)), "bs_lookup")
+    return out, count
+
+
+def bs_lookup_codes(col: Column, bits, out=None, out_cap: int | None = None, count=None, workspace=None,
+                    stream=None):
+    import torch
+    if out is None:
+        out = torch.empty(max(1, col.n if out_cap is None else out_cap), dtype=torch.int64, device="cuda")
+    cap = out.numel() if out_cap is None else int(out_cap)
+    if count is None:
+        count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(lib().bs_lookup_codes(col.handle, _dptr(bits), _dptr(out), cap, _dptr(count), _dptr(workspace),
+                                 ws_bytes, _stream(stream)), "bs_lookup_codes")
+    return out, count
+
+
+def bs_lookup_rowids(col: Column, rowids, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty(max(1, rowids.numel()), dtype=torch.int32, device="cuda")
+    _check(lib().bs_lookup_rowids(col.handle, _dptr(rowids), rowids.numel(), _dptr(out), _stream(stream)),
+           "bs_lookup_rowids")
+    return out
+
+
+# ----------------------------------------------------------------- advisor
+def bs_advise_layout(values, mode: int = ADVISE_BYTES_MODEL, **opts) -> dict:
+    v = _np(values, np.int32)
+    o, keep = _opts(**opts)
+    a = bs_advice()
+    _check(lib().bs_advise_layout(v.ctypes.data if v.size else None, v.size, int(mode), ctypes.byref(o),
+                                  ctypes.byref(a)), "bs_advise_layout")
+    k = a.n_points
+    return {"layout": {0: "bitpacked", 1: "byteslice", 2: "ppvbs"}[a.layout], "auc_byteslice": a.auc_byteslice,
+            "auc_ppvbs": a.auc_ppvbs, "selectivity": list(a.selectivity[:k]),
+            "cost_byteslice": list(a.cost_byteslice[:k]), "cost_ppvbs": list(a.cost_ppvbs[:k])}
+
+
+# ------------------------------------------------------------- diagnostics
+def bs_strerror(status: int) -> str:
+    return lib().bs_strerror(int(status)).decode()
+
+
+def bs_last_device_error() -> int:
+    return int(lib().bs_last_device_error())
+
+
+def bs_version() -> str:
+    return lib().bs_version().decode()

@@ -1,0 +1,422 @@
+// Scan kernels for sm_103a: PP-VBS (Algorithm 3), ByteSlice (Section 2.5) and
+// Bit-Packed (Section 2.3), with optional seeding by a previous result bit
+// vector (the pipelined conjunction of Section 3.3.1).
+//
+// One warp owns one 1024-row tile at a time (grid-stride over tiles); lane L
+// owns rows 32L..32L+31 of the tile and produces result word L.
+//
+// Byte compare (the counterpart of the paper's cmpgt/cmpeq + movemask): each
+// 32-bit word holds 4 row bytes; a SWAR sequence yields, in the most
+// significant bit of every byte, "byte < c" and "byte == c" for the literal
+// byte c, unsigned. The dense slices are stored so that word w byte b of a
+// lane's 32 bytes is row 8b + w, hence OR-ing word w shifted right by 7 - w
+// gathers the 32 flags of a lane into a row-ordered result word.
+//
+// Early stop (Section 2.5, Lemma 1): after byte 1 a lane keeps, per literal,
+// LT (decided smaller) and EQ (equal so far) masks. Deeper bytes are touched
+// only while some lane of the warp still has EQ rows (__any_sync). For PP-VBS a
+// row's byte j exists iff bit j of mask M_j is set; the mask words are read
+// only for 256-row groups (one 32-byte sector of M_j) that contain pending
+// rows, and each pending row's byte is fetched from the packed slice BS_j at
+// off_j[group] + (popcounts of the group's earlier mask words) + rank in its
+// word. Rows that end before the literal are smaller, rows that continue past
+// it are larger (the code tail after a shared prefix is never zero).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "kernels.h"
+
+namespace bs {
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr int kScanThreads = 256;
+
+struct DLit {
+    uint32_t len;   // bytes in the literal code
+    uint32_t pad_;
+    uint64_t left;  // code left-aligned in 64 bits: byte j (1-based) = left >> (64 - 8j)
+};
+
+struct ScanK {
+    const uint8_t *dense;      // BS_1 (PP-VBS) or slice 1 (ByteSlice)
+    uint64_t slice_bytes;      // ByteSlice: distance between slices
+    const uint32_t *mask[kMaxCodeBytes + 1];
+    const uint32_t *off[kMaxCodeBytes + 1];
+    const uint8_t *deep[kMaxCodeBytes + 1];
+    uint64_t deep_len[kMaxCodeBytes + 1];
+    const uint32_t *packed;
+    uint64_t n;
+    uint32_t n_tiles;
+    int32_t K;                 // PP-VBS longest code; ByteSlice slice count
+    int32_t k;                 // Bit-Packed code bits
+    int32_t op;
+    int32_t has_deeper;
+    int32_t fill_all;          // fill kernel: 1 = every valid (seeded) row, 0 = none
+    DLit lit[2];
+    uint64_t lo, hi;           // Bit-Packed: code range of the predicate
+    int32_t invert;            // Bit-Packed: result = !(lo <= code <= hi)
+    const uint32_t *seed;
+    uint32_t *out;
+    uint32_t *status;
+};
+
+__device__ __forceinline__ uint4 ld_stream_v4(const uint8_t *p) {
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_stream(uint32_t *p, uint32_t v) {
+    asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t valid_mask(uint64_t row0, uint64_t n) {
+    if (row0 + 32 <= n) return kFull;
+    if (row0 >= n) return 0u;
+    return (1u << (uint32_t)(n - row0)) - 1u;
+}
+
+__device__ __forceinline__ uint32_t lit_byte(const DLit &l, int j) {  // j = 1..8
+    return (uint32_t)(l.left >> (64 - 8 * j)) & 0xFFu;
+}
+
+// Constants of the SWAR compare against one literal byte c.
+struct ByteCmp {
+    uint32_t add;  // per byte 0x80 - (c & 0x7f): low-7-bit compare lands in bit 7
+    uint32_t sel;  // all ones if c < 0x80 (x >= c iff high bit or low bits >= c)
+    uint32_t rep;  // c in every byte
+};
+
+__device__ __forceinline__ ByteCmp make_cmp(uint32_t c) {
+    ByteCmp k;
+    k.add = (0x80u - (c & 0x7Fu)) * 0x01010101u;
+    k.sel = (c & 0x80u) ? 0u : kFull;
+    k.rep = c * 0x01010101u;
+    return k;
+}
+
+// Bit 7 of every byte: lt = (x_byte < c), eq = (x_byte == c), unsigned.
+__device__ __forceinline__ void cmp_word(uint32_t x, const ByteCmp &k, uint32_t &lt, uint32_t &eq) {
+    uint32_t y = (x & 0x7F7F7F7Fu) + k.add;
+    uint32_t ge = (y & x) | ((y | x) & k.sel);
+    lt = ~ge & 0x80808080u;
+    uint32_t t = x ^ k.rep;
+    uint32_t z = (t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;
+    eq = ~(z | t) & 0x80808080u;
+}
+
+__device__ __forceinline__ uint32_t gather8(const uint32_t m[8]) {
+    return (m[0] >> 7) | (m[1] >> 6) | (m[2] >> 5) | (m[3] >> 4) | (m[4] >> 3) | (m[5] >> 2) | (m[6] >> 1) | m[7];
+}
+
+__device__ __forceinline__ void cmp32(const uint32_t x[8], const ByteCmp &k, uint32_t &LT, uint32_t &EQ) {
+    uint32_t lt[8], eq[8];
+#pragma unroll
+    for (int w = 0; w < 8; w++) cmp_word(x[w], k, lt[w], eq[w]);
+    LT = gather8(lt);
+    EQ = gather8(eq);
+}
+
+__device__ __forceinline__ void load_lane32(const uint8_t *tile, uint32_t lane, uint32_t x[8]) {
+    uint4 v0 = ld_stream_v4(tile + lane * 16u);
+    uint4 v1 = ld_stream_v4(tile + 512u + lane * 16u);
+    x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+    x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+}
+
+__device__ __forceinline__ uint32_t final_bits(int op, uint32_t sd, uint32_t LT1, uint32_t EQ1, uint32_t LT2,
+                                               uint32_t EQ2) {
+    switch (op) {
+    case BS_LT: return LT1;
+    case BS_LE: return LT1 | EQ1;
+    case BS_GT: return sd & ~(LT1 | EQ1);
+    case BS_GE: return sd & ~LT1;
+    case BS_EQ: return EQ1;
+    case BS_NE: return sd & ~EQ1;
+    default: return sd & ~LT1 & (LT2 | EQ2);  // BETWEEN
+    }
+}
+
+// ------------------------------------------------------- PP-VBS levels >= 2
+template <int NLIT>
+__device__ __noinline__ void vbs_deeper(const ScanK &a, uint32_t t, uint32_t lane, uint32_t &LT1, uint32_t &EQ1,
+                                        uint32_t &LT2, uint32_t &EQ2) {
+    const int K = a.K;
+    const int l1 = (int)a.lit[0].len;
+    const int l2 = NLIT == 2 ? (int)a.lit[1].len : 0;
+    bool done1 = false, done2 = (NLIT == 1);
+    const int jend = min(max(l1, l2) + 1, K);
+    const uint64_t wbase = (uint64_t)t * kTileWords;
+    for (int j = 2; j <= jend; j++) {
+        uint32_t pend = (done1 ? 0u : EQ1) | (done2 ? 0u : EQ2);
+        if (!__any_sync(kFull, pend != 0u)) break;
+        // M_j only for 256-row groups (8 lanes) holding a pending row
+        uint32_t bal = __ballot_sync(kFull, pend != 0u);
+        uint32_t gact = (bal >> (lane & 24u)) & 0xFFu;
+        uint32_t mj = gact ? __ldg(a.mask[j] + wbase + lane) : 0u;
+        if (!done1) {
+            if (j <= l1) { LT1 |= EQ1 & ~mj; EQ1 &= mj; }   // row ends first: smaller
+            else { EQ1 &= ~mj; done1 = true; }             // row continues: larger; else equal
+        }
+        if (NLIT == 2 && !done2) {
+            if (j <= l2) { LT2 |= EQ2 & ~mj; EQ2 &= mj; }
+            else { EQ2 &= ~mj; done2 = true; }
+        }
+        uint32_t need = (done1 ? 0u : EQ1) | (done2 ? 0u : EQ2);
+        if (!__any_sync(kFull, need != 0u)) continue;
+        // rank of each byte in BS_j: exclusive prefix of popcounts inside the group
+        uint32_t cnt = __popc(mj), incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+            uint32_t v = __shfl_up_sync(kFull, incl, d);
+            if ((lane & 7u) >= (uint32_t)d) incl += v;
+        }
+        if (need) {
+            const uint64_t base = (uint64_t)__ldg(a.off[j] + (uint64_t)t * kGroupsPerTile + (lane >> 3)) + (incl - cnt);
+            const uint8_t *deep = a.deep[j];
+            const uint64_t dlen = a.deep_len[j];
+            const uint32_t c1 = lit_byte(a.lit[0], j);
+            const uint32_t c2 = NLIT == 2 ? lit_byte(a.lit[1], j) : 0u;
+            uint32_t bits = need;
+            while (bits) {
+                const uint32_t r = __ffs(bits) - 1;
+                const uint32_t bit = 1u << r;
+                bits &= bits - 1;
+                const uint64_t idx = base + __popc(mj & (bit - 1u));
+                uint32_t byte = 0;
+                if (idx < dlen) {
+                    byte = __ldg(deep + idx);
+                } else {
+                    atomicOr(a.status, kStatusBounds);
+                }
+                if (!done1 && (EQ1 & bit)) {
+                    if (byte < c1) { LT1 |= bit; EQ1 &= ~bit; }
+                    else if (byte > c1) EQ1 &= ~bit;
+                }
+                if (NLIT == 2 && !done2 && (EQ2 & bit)) {
+                    if (byte < c2) { LT2 |= bit; EQ2 &= ~bit; }
+                    else if (byte > c2) EQ2 &= ~bit;
+                }
+            }
+        }
+    }
+    // a literal longer than every stored code: an equal prefix means a shorter row
+    if (!done1 && l1 > K) { LT1 |= EQ1; EQ1 = 0; }
+    if (NLIT == 2 && !done2 && l2 > K) { LT2 |= EQ2; EQ2 = 0; }
+}
+
+// ---------------------------------------------------- ByteSlice slices >= 2
+template <int NLIT>
+__device__ __noinline__ void bsl_deeper(const ScanK &a, uint32_t t, uint32_t lane, uint32_t &LT1, uint32_t &EQ1,
+                                        uint32_t &LT2, uint32_t &EQ2) {
+    for (int j = 2; j <= a.K; j++) {
+        const uint32_t pend = EQ1 | EQ2;
+        if (!__any_sync(kFull, pend != 0u)) break;
+        if (pend) {
+            uint32_t x[8];
+            load_lane32(a.dense + (uint64_t)(j - 1) * a.slice_bytes + (uint64_t)t * kTileRows, lane, x);
+            uint32_t lt, eq;
+            cmp32(x, make_cmp(lit_byte(a.lit[0], j)), lt, eq);
+            LT1 |= EQ1 & lt;
+            EQ1 &= eq;
+            if (NLIT == 2) {
+                cmp32(x, make_cmp(lit_byte(a.lit[1], j)), lt, eq);
+                LT2 |= EQ2 & lt;
+                EQ2 &= eq;
+            }
+        }
+    }
+}
+
+template <bool VBS, int NLIT>
+__global__ void __launch_bounds__(kScanThreads) scan_dense_kernel(const ScanK a) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const ByteCmp k1 = make_cmp(lit_byte(a.lit[0], 1));
+    const ByteCmp k2 = make_cmp(lit_byte(a.lit[NLIT - 1], 1));
+    for (uint32_t t = gw; t < a.n_tiles; t += nw) {
+        const uint64_t w = (uint64_t)t * kTileWords + lane;
+        uint32_t sd = valid_mask(w * 32u, a.n);  // 0 for words at or past ceil(n/32)
+        if (a.seed && sd) sd &= __ldg(a.seed + w);
+        uint32_t LT1 = 0, EQ1 = 0, LT2 = 0, EQ2 = 0;
+        if (sd) {
+            uint32_t x[8];
+            load_lane32(a.dense + (uint64_t)t * kTileRows, lane, x);
+            cmp32(x, k1, LT1, EQ1);
+            LT1 &= sd;
+            EQ1 &= sd;
+            if (NLIT == 2) {
+                cmp32(x, k2, LT2, EQ2);
+                LT2 &= sd;
+                EQ2 &= sd;
+            }
+        }
+        if (a.has_deeper && __any_sync(kFull, (EQ1 | EQ2) != 0u)) {
+            if (VBS) vbs_deeper<NLIT>(a, t, lane, LT1, EQ1, LT2, EQ2);
+            else bsl_deeper<NLIT>(a, t, lane, LT1, EQ1, LT2, EQ2);
+        }
+        if (w * 32u < a.n) st_stream(a.out + w, final_bits(a.op, sd, LT1, EQ1, LT2, EQ2));
+    }
+}
+
+// ------------------------------------------------------------ Bit-Packed
+// Round m of a tile evaluates rows 32m..32m+31: their codes fill exactly k
+// stream words starting at word t*32k + m*k, which lanes 0..k-1 load together;
+// each lane then funnel-shifts its code out of two neighbouring words received
+// by shuffle, and one ballot gives result word m.
+__global__ void __launch_bounds__(kScanThreads) scan_packed_kernel(const ScanK a) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t k = (uint32_t)a.k;
+    const uint32_t kmask = k == 32 ? kFull : ((1u << k) - 1u);
+    const uint32_t lobit = lane * k;
+    const uint32_t src = lobit >> 5, sh = lobit & 31u;
+    for (uint32_t t = gw; t < a.n_tiles; t += nw) {
+        const uint64_t w = (uint64_t)t * kTileWords + lane;
+        uint32_t sdw = valid_mask(w * 32u, a.n);
+        if (a.seed && sdw) sdw &= __ldg(a.seed + w);
+        uint32_t res = 0;
+        const uint32_t *tw = a.packed + (uint64_t)t * kTileWords * k;
+#pragma unroll 4
+        for (uint32_t m = 0; m < 32u; m++) {
+            const uint32_t sm = __shfl_sync(kFull, sdw, m);
+            if (sm == 0u) continue;
+            const uint32_t *rw = tw + m * k;
+            uint32_t code;
+            if (k == 32u) {
+                code = __ldg(rw + lane);
+            } else {
+                const uint32_t word = lane < k ? __ldg(rw + lane) : 0u;
+                const uint32_t lo = __shfl_sync(kFull, word, src);
+                const uint32_t hi = __shfl_sync(kFull, word, (src + 1u) & 31u);
+                code = __funnelshift_r(lo, hi, sh) & kmask;
+            }
+            const bool in = (uint64_t)code >= a.lo && (uint64_t)code <= a.hi;
+            const uint32_t b = __ballot_sync(kFull, in != (a.invert != 0)) & sm;
+            if (lane == m) res = b;
+        }
+        if (w * 32u < a.n) st_stream(a.out + w, res);
+    }
+}
+
+// Constant predicates (literal outside the dictionary): every valid seeded row,
+// or none.
+__global__ void scan_fill_kernel(const ScanK a) {
+    const uint64_t nwords = (a.n + 31) / 32;
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nwords;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t v = 0;
+        if (a.fill_all) {
+            v = valid_mask(w * 32u, a.n);
+            if (a.seed) v &= a.seed[w];
+        }
+        a.out[w] = v;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+template <class F>
+int grid_for(F kernel, uint32_t n_tiles, int device) {
+    const int per_sm = blocks_per_sm((const void *)kernel, kScanThreads, 0, device);
+    const uint64_t want = ((uint64_t)n_tiles + (kScanThreads / 32) - 1) / (kScanThreads / 32);
+    const uint64_t cap = (uint64_t)sm_count(device) * (uint64_t)per_sm;
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, cap));
+}
+
+DLit make_dlit(const LitCode &l) {
+    DLit d{};
+    d.len = l.len;
+    d.left = l.len >= 8 ? l.code : (l.code << (8 * (8 - l.len)));
+    return d;
+}
+
+}  // namespace
+
+int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_t *d_out, cudaStream_t s) {
+    if (c.n == 0) return BS_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BS_ERR_CUDA;
+    ScanK a{};
+    a.n = c.n;
+    a.n_tiles = c.n_tiles;
+    a.seed = d_seed;
+    a.out = d_out;
+    a.status = status_word();
+    if (!a.status) return BS_ERR_CUDA;
+    a.op = p.op;
+    if (p.mode != Pred::kNormal) {
+        a.fill_all = p.mode == Pred::kAll;
+        uint64_t nwords = (uint64_t)c.n_tiles * kTileWords;
+        int grid = (int)std::min<uint64_t>((nwords + 255) / 256, (uint64_t)sm_count(dev) * 8);
+        scan_fill_kernel<<<std::max(grid, 1), 256, 0, s>>>(a);
+        return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+    }
+    const int nlit = p.op == BS_BETWEEN ? 2 : 1;
+    if (c.layout == BS_BITPACKED) {
+        a.packed = c.d_packed;
+        a.k = c.k;
+        const uint64_t c1 = p.lit[0].code, c2 = p.lit[1].code;
+        const uint64_t top = (c.k >= 64) ? ~0ull : ((1ull << c.k) - 1);
+        a.invert = 0;
+        switch (p.op) {
+        case BS_LT:
+            if (c1 == 0) { a.lo = 1; a.hi = 0; }  // empty range
+            else { a.lo = 0; a.hi = c1 - 1; }
+            break;
+        case BS_LE: a.lo = 0; a.hi = c1; break;
+        case BS_GT: a.lo = c1 + 1; a.hi = top; break;
+        case BS_GE: a.lo = c1; a.hi = top; break;
+        case BS_EQ: a.lo = c1; a.hi = c1; break;
+        case BS_NE: a.lo = c1; a.hi = c1; a.invert = 1; break;
+        default: a.lo = c1; a.hi = c2; break;
+        }
+        int grid = grid_for(scan_packed_kernel, c.n_tiles, dev);
+        scan_packed_kernel<<<grid, kScanThreads, 0, s>>>(a);
+        return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+    }
+    a.dense = c.d_dense;
+    a.slice_bytes = c.dense_slice_bytes();
+    LitCode l0 = p.lit[0], l1 = nlit == 2 ? p.lit[1] : p.lit[0];
+    if (c.layout == BS_BYTESLICE) {
+        // ByteSlice bytes are those of the code left-aligned in S bytes
+        l0.code <<= (8 * c.S - c.k);
+        l1.code <<= (8 * c.S - c.k);
+        l0.len = l1.len = (uint32_t)c.S;
+    }
+    a.lit[0] = make_dlit(l0);
+    a.lit[1] = make_dlit(l1);
+    if (c.layout == BS_PPVBS) {
+        a.K = c.K;
+        for (int j = 2; j <= c.K; j++) {
+            a.mask[j] = c.d_mask[j];
+            a.off[j] = c.d_off[j];
+            a.deep[j] = c.d_deep[j];
+            a.deep_len[j] = c.deep_len[j];
+        }
+        int lmax = (int)std::max(a.lit[0].len, a.lit[1].len);
+        a.has_deeper = (c.K >= 2 || lmax >= 2) ? 1 : 0;
+        if (nlit == 2) {
+            scan_dense_kernel<true, 2><<<grid_for(scan_dense_kernel<true, 2>, c.n_tiles, dev), kScanThreads, 0, s>>>(a);
+        } else {
+            scan_dense_kernel<true, 1><<<grid_for(scan_dense_kernel<true, 1>, c.n_tiles, dev), kScanThreads, 0, s>>>(a);
+        }
+    } else {
+        a.K = c.S;
+        a.has_deeper = c.S >= 2 ? 1 : 0;
+        if (nlit == 2) {
+            scan_dense_kernel<false, 2><<<grid_for(scan_dense_kernel<false, 2>, c.n_tiles, dev), kScanThreads, 0, s>>>(a);
+        } else {
+            scan_dense_kernel<false, 1><<<grid_for(scan_dense_kernel<false, 1>, c.n_tiles, dev), kScanThreads, 0, s>>>(a);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
+}  // namespace bs
