@@ -191,6 +191,48 @@ int bs_lookup_codes(const bs_column *col, const uint32_t *d_bits, uint64_t *d_co
 int bs_lookup_rowids(const bs_column *col, const uint32_t *d_rowids, uint64_t m, int32_t *d_out,
                      void *stream);
 
+/* ------------------------------------------------ effective-bytes counter */
+
+/* Bytes one scan must move at the kernels' granularity (32-byte sectors,
+ * 256-row mask groups, 1024-row tiles), replayed on the host: the dense slice
+ * sectors of lanes with rows to scan, then -- only for rows still equal to the
+ * literal (early stop, Section 2.5 and Lemma 1) -- the M_j sectors of their
+ * groups, the off_j entries and the BS_j sectors of the bytes compared (PP-VBS)
+ * or the next slice's sectors (ByteSlice); Bit-Packed reads its whole stream.
+ * paper_model_bytes is Algorithm 3 as printed (every mask word of levels
+ * 2..min(l+1,K) loaded eagerly, 32-byte slice loads). Needs the host copy of
+ * the layout (keep_host or host_only). h_seed: optional seed bit vector (host). */
+typedef struct {
+    uint64_t bytes;              /* dense + mask + offset + deep + result */
+    uint64_t dense_bytes;
+    uint64_t mask_bytes;
+    uint64_t offset_bytes;
+    uint64_t deep_bytes;
+    uint64_t result_bytes;       /* result words written (+ seed words read) */
+    uint64_t paper_model_bytes;
+    uint64_t pending_rows[9];    /* rows still undecided entering byte j */
+    uint64_t sampled_tiles;
+} bs_scan_bytes_t;
+
+int bs_scan_bytes(const bs_column *col, bs_op op, int32_t lit, int32_t lit2, const uint32_t *h_seed,
+                  bs_scan_bytes_t *out);
+
+/* Bytes one lookup must move: the bit vector once, 4 bytes per output value and
+ * the distinct sectors of every gathered byte, mask group and offset entry
+ * (decode tables are assumed cache-resident). h_bits: host bit vector. */
+typedef struct {
+    uint64_t bytes;
+    uint64_t selected;
+    uint64_t bits_bytes;
+    uint64_t out_bytes;
+    uint64_t dense_bytes;
+    uint64_t mask_bytes;
+    uint64_t offset_bytes;
+    uint64_t deep_bytes;
+} bs_lookup_bytes_t;
+
+int bs_lookup_bytes(const bs_column *col, const uint32_t *h_bits, bs_lookup_bytes_t *out);
+
 /* ---------------------------------------------------- layout advisor */
 
 #define BS_ADVISE_TIMED 0        /* Algorithm 5: time 100 scans per layout on the GPU */

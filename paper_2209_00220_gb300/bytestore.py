@@ -43,6 +43,17 @@ class bs_pred(ctypes.Structure):
     _fields_ = [("col", _vp), ("op", _i32), ("lit", _i32), ("lit2", _i32), ("reserved", _i32)]
 
 
+class bs_scan_bytes_t(ctypes.Structure):
+    _fields_ = [("bytes", _u64), ("dense_bytes", _u64), ("mask_bytes", _u64), ("offset_bytes", _u64),
+                ("deep_bytes", _u64), ("result_bytes", _u64), ("paper_model_bytes", _u64),
+                ("pending_rows", _u64 * 9), ("sampled_tiles", _u64)]
+
+
+class bs_lookup_bytes_t(ctypes.Structure):
+    _fields_ = [("bytes", _u64), ("selected", _u64), ("bits_bytes", _u64), ("out_bytes", _u64),
+                ("dense_bytes", _u64), ("mask_bytes", _u64), ("offset_bytes", _u64), ("deep_bytes", _u64)]
+
+
 class bs_advice(ctypes.Structure):
     _fields_ = [("layout", _i32), ("n_points", _i32), ("auc_byteslice", ctypes.c_double),
                 ("auc_ppvbs", ctypes.c_double), ("selectivity", ctypes.c_double * 100),
@@ -65,6 +76,8 @@ _SIGS = {
     "bs_lookup_codes": ([_vp, _vp, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "bs_lookup_rowids": ([_vp, _vp, _u64, _vp, _vp], _i32),
     "bs_advise_layout": ([_vp, _u64, _i32, _vp, _vp], _i32),
+    "bs_scan_bytes": ([_vp, _i32, _i32, _i32, _vp, _vp], _i32),
+    "bs_lookup_bytes": ([_vp, _vp, _vp], _i32),
     "bs_strerror": ([_i32], ctypes.c_char_p),
     "bs_last_device_error": ([], _i32),
     "bs_version": ([], ctypes.c_char_p),
@@ -302,6 +315,34 @@ def bs_lookup_rowids(col: Column, rowids, out=None, stream=None):
     _check(lib().bs_lookup_rowids(col.handle, _dptr(rowids), rowids.numel(), _dptr(out), _stream(stream)),
            "bs_lookup_rowids")
     return out
+
+
+# ------------------------------------------------- effective-bytes counter
+def _struct_dict(st) -> dict:
+    out = {}
+    for name, _ in st._fields_:
+        v = getattr(st, name)
+        out[name] = list(v) if hasattr(v, "__len__") else int(v)
+    return out
+
+
+def bs_scan_bytes(col: Column, op: str, lit: int, lit2: int = 0, seed=None) -> dict:
+    """Bytes the scan must move at the kernels' granularity (host replay).
+    seed: optional host numpy uint32 bit vector."""
+    r = bs_scan_bytes_t()
+    sd = None if seed is None else _np(seed, np.uint32)
+    _check(lib().bs_scan_bytes(col.handle, OPS[op], int(lit), int(lit2), None if sd is None else sd.ctypes.data,
+                               ctypes.byref(r)), "bs_scan_bytes")
+    return _struct_dict(r)
+
+
+def bs_lookup_bytes(col: Column, bits) -> dict:
+    """bits: host numpy uint32 bit vector."""
+    r = bs_lookup_bytes_t()
+    b = _np(bits, np.uint32)
+    _check(lib().bs_lookup_bytes(col.handle, b.ctypes.data if b.size else None, ctypes.byref(r)),
+           "bs_lookup_bytes")
+    return _struct_dict(r)
 
 
 # ----------------------------------------------------------------- advisor

@@ -76,6 +76,7 @@ struct Column {
     std::vector<int32_t> dict;  // sorted distinct values (dictionary)
     std::vector<uint64_t> dcode;  // PP-VBS: code of dict[i] (unpadded)
     std::vector<uint8_t> dlen;    // PP-VBS: its length in bytes
+    std::vector<uint64_t> dcount; // rows holding dict[i] (observed dictionaries)
     bool root_leaf = true;        // PP-VBS decode: the root node is a leaf
     std::vector<uint32_t> trie;   // PP-VBS decode tables, kTrieNodeWords per internal node
 
@@ -111,6 +112,11 @@ int encode_raw(const uint64_t *codes, const uint8_t *lens, uint64_t n, bs_layout
 int rewrite_literal(const Column &c, int op, int32_t lit, int32_t lit2, KPred &out);
 int make_code_pred(const Column &c, int op, uint64_t code, int len, uint64_t code2, int len2, KPred &out);
 int resolve_threads(int requested);
+
+// effective-bytes counter (bytes_model.cpp); tile_stride > 1 samples every
+// tile_stride-th tile and scales up
+int scan_bytes(const Column &c, const KPred &p, const uint32_t *seed, uint64_t tile_stride, bs_scan_bytes_t *out);
+int lookup_bytes(const Column &c, const uint32_t *bits, bs_lookup_bytes_t *out);
 
 // device side (column.cu)
 int upload_column(Column &c);

@@ -432,6 +432,7 @@ int encode_values(const int32_t *values, uint64_t n, bs_layout layout, const bs_
             int rc = build_dictionary(values, n, T, c.dict, Q, ridx);
             if (rc) return rc;
             ppe_numerical(Q, c.dcode, c.dlen, c.trie, c.root_leaf, T);
+            c.dcount = Q;
             c.K = 1;
             for (uint8_t l : c.dlen) c.K = std::max<int>(c.K, l);
             const uint64_t *dc = c.dcode.data();

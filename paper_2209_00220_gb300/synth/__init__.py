@@ -187,31 +187,44 @@ def _sample(values: np.ndarray, seed: int, k: int = 1 << 20) -> np.ndarray:
 
 
 def pick_literals(values: np.ndarray, op: str, target: float, seed: int = 0):
-    """Literals (lit, lit2) aiming at selectivity ``target`` for ``op``.
+    """Literals (lit, lit2) aiming at selectivity ``target`` for ``op``, read off
+    a bounded seeded sample (exact targets are impossible on discrete data):
 
-    lt/le/gt/ge: a sample quantile. eq/ne: the sampled value whose frequency is
-    closest to target (eq) or 1 - target (ne). between: [q0, q0 + target]
-    quantiles with q0 seeded. Values are plain int32; lit2 is 0 unless between.
+    lt: the smallest value c with share(v < c) >= target; le: the smallest c with
+    share(v <= c) >= target; ge / gt: the largest c with share(v >= c) resp.
+    share(v > c) >= target; eq: the value whose share is closest to target;
+    ne: closest to 1 - target; between: lo at a seeded quantile, hi the smallest
+    value with share(lo <= v <= hi) >= target. lit2 is 0 unless between.
     """
     smp = _sample(values, seed)
     m = smp.size
-    int32 = lambda x: int(np.clip(x, -(1 << 31), (1 << 31) - 1))
-    if op in ("lt", "ge"):
-        q = target if op == "lt" else 1.0 - target
-        c = smp[min(m - 1, int(q * m))]
-        return int32(c), 0
-    if op in ("le", "gt"):
-        q = target if op == "le" else 1.0 - target
-        i = int(q * m) - 1
-        return (int32(smp[0] - 1) if i < 0 else int32(smp[min(m - 1, i)])), 0
+    u, cnt = np.unique(smp, return_counts=True)
+    below = np.concatenate([[0], np.cumsum(cnt)[:-1]])  # rows < u[i]
+    upto = below + cnt                                  # rows <= u[i]
+    want = target * m
+    clip = lambda x: int(np.clip(x, -(1 << 31), (1 << 31) - 1))
+    if op == "lt":
+        i = np.flatnonzero(below >= want)
+        return (clip(u[i[0]]) if i.size else clip(u[-1] + 1)), 0
+    if op == "le":
+        i = np.flatnonzero(upto >= want)
+        return (clip(u[i[0]]) if i.size else clip(u[-1])), 0
+    if op == "ge":
+        i = np.flatnonzero(m - below >= want)
+        return (clip(u[i[-1]]) if i.size else clip(u[0])), 0
+    if op == "gt":
+        i = np.flatnonzero(m - upto >= want)
+        return (clip(u[i[-1]]) if i.size else clip(u[-1])), 0
     if op in ("eq", "ne"):
-        u, cnt = np.unique(smp, return_counts=True)
         f = cnt / m
-        want = target if op == "eq" else 1.0 - target
-        return int32(u[int(np.argmin(np.abs(f - want)))]), 0
+        w = target if op == "eq" else 1.0 - target
+        return clip(u[int(np.argmin(np.abs(f - w)))]), 0
     if op == "between":
         q0 = float(u64(seed, 123, 1)[0] >> np.uint64(11)) / float(1 << 53) * max(0.0, 1.0 - target)
-        lo = smp[min(m - 1, int(q0 * m))]
-        hi = smp[min(m - 1, max(0, int((q0 + target) * m) - 1))]
-        return int32(lo), int32(max(lo, hi))
+        lo_i = int(np.searchsorted(below, q0 * m, side="right")) - 1
+        lo_i = max(0, min(lo_i, u.size - 1))
+        got = upto - below[lo_i]
+        j = np.flatnonzero((np.arange(u.size) >= lo_i) & (got >= want))
+        hi_i = int(j[0]) if j.size else u.size - 1
+        return clip(u[lo_i]), clip(u[hi_i])
     raise ValueError(op)
