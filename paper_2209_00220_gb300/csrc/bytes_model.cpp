@@ -65,11 +65,13 @@ struct Acc {
 // Resolve one row against one literal: the deepest level that still needs the
 // row's mask bit (pend_to) and the deepest level whose byte is read (byte_to).
 // Levels are 1-based; 1 means only BS_1 was needed.
-void replay_row(const uint8_t *code, int L, const Lit &lit, int K, int &pend_to, int &byte_to) {
+// need_eq: the predicate distinguishes "equal" from "larger" for this literal
+// (otherwise rows equal after the literal's last byte are never read again).
+void replay_row(const uint8_t *code, int L, const Lit &lit, int K, bool need_eq, int &pend_to, int &byte_to) {
     pend_to = 1;
     byte_to = 1;
     if (code[1] != lit.b[1]) return;
-    const int jend = std::min(lit.len + 1, K);
+    const int jend = need_eq ? std::min(lit.len + 1, K) : std::min(lit.len, K);
     for (int j = 2; j <= jend; j++) {
         pend_to = j;                       // mask M_j consulted
         if (L < j) return;                 // row ended: decided
@@ -170,7 +172,8 @@ int scan_bytes(const Column &c, const KPred &p, const uint32_t *seed, uint64_t t
                 for (int i = 0; i < nlit; i++) {
                     int pt, bt;
                     if (c.layout == BS_PPVBS) {
-                        replay_row(code, L, lits[i], K, pt, bt);
+                        const bool need_eq = i == 1 || !(p.op == BS_LT || p.op == BS_GE || p.op == BS_BETWEEN);
+                        replay_row(code, L, lits[i], K, need_eq, pt, bt);
                     } else {
                         pt = 1;
                         for (int s = 1; s <= K; s++) {

@@ -6,11 +6,15 @@
 // owns rows 32L..32L+31 of the tile and produces result word L.
 //
 // Byte compare (the counterpart of the paper's cmpgt/cmpeq + movemask): each
-// 32-bit word holds 4 row bytes; a SWAR sequence yields, in the most
-// significant bit of every byte, "byte < c" and "byte == c" for the literal
-// byte c, unsigned. The dense slices are stored so that word w byte b of a
-// lane's 32 bytes is row 8b + w, hence OR-ing word w shifted right by 7 - w
-// gathers the 32 flags of a lane into a row-ordered result word.
+// 32-bit word holds 4 row bytes. With r = x & 0x7f7f7f7f, adding
+// 0x80 - (k & 0x7f) to every byte puts "low 7 bits >= k's low 7 bits" into bit
+// 7 without carries between bytes; AND-ing (k >= 0x80) or OR-ing (k < 0x80)
+// with x's own bit 7 then gives "x >= k" unsigned in bit 7 of every byte (one
+// LOP3 when the high bit of k is a template constant). "x == c" is
+// ge(c) & ~ge(c+1) (c + 1 = 256 never matches). The dense slices are stored so
+// that word w byte b of a lane's 32 bytes is row 8b + w, hence OR-ing word w
+// shifted right by 7 - w gathers the 32 flags of a lane into a row-ordered
+// result word.
 //
 // Early stop (Section 2.5, Lemma 1): after byte 1 a lane keeps, per literal,
 // LT (decided smaller) and EQ (equal so far) masks. Deeper bytes are touched
@@ -21,10 +25,18 @@
 // off_j[group] + (popcounts of the group's earlier mask words) + rank in its
 // word. Rows that end before the literal are smaller, rows that continue past
 // it are larger (the code tail after a shared prefix is never zero).
+// When the predicate only needs "smaller" for a literal (v < c, v >= c and the
+// lower end of BETWEEN), rows still equal after the literal's last byte are
+// settled (equal or larger: never smaller), so level l + 1 is not read; with a
+// one-byte literal the EQ mask is not even formed.
+//
+// Unseeded scans stream slice 1 through a 3-stage cp.async ring in shared
+// memory per warp, so two tiles are in flight while one is resolved. Each
+// lane reads back only the 32 bytes it copied itself, so no barrier is needed
+// beyond cp.async.wait_group.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "kernels.h"
 
@@ -32,12 +44,16 @@ namespace bs {
 namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kMsb = 0x80808080u;
+constexpr uint32_t kLow7 = 0x7F7F7F7Fu;
 constexpr int kScanThreads = 256;
+constexpr int kScanWarps = kScanThreads / 32;
+constexpr int kStages = 3;
 
 struct DLit {
-    uint32_t len;   // bytes in the literal code
-    uint32_t pad_;
-    uint64_t left;  // code left-aligned in 64 bits: byte j (1-based) = left >> (64 - 8j)
+    uint32_t len;      // bytes in the literal code
+    int32_t jend;      // deepest level whose masks/bytes can change the result
+    uint64_t left;     // code left-aligned in 64 bits: byte j (1-based) = left >> (64 - 8j)
 };
 
 struct ScanK {
@@ -53,7 +69,6 @@ struct ScanK {
     int32_t K;                 // PP-VBS longest code; ByteSlice slice count
     int32_t k;                 // Bit-Packed code bits
     int32_t op;
-    int32_t has_deeper;
     int32_t fill_all;          // fill kernel: 1 = every valid (seeded) row, 0 = none
     DLit lit[2];
     uint64_t lo, hi;           // Bit-Packed: code range of the predicate
@@ -75,6 +90,13 @@ __device__ __forceinline__ void st_stream(uint32_t *p, uint32_t v) {
     asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t smem_addr, const uint8_t *g) {
+    asm volatile("cp.async.cg.shared.global.L2::256B [%0], [%1], 16;" ::"r"(smem_addr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ uint32_t valid_mask(uint64_t row0, uint64_t n) {
     if (row0 + 32 <= n) return kFull;
     if (row0 >= n) return 0u;
@@ -85,40 +107,53 @@ __device__ __forceinline__ uint32_t lit_byte(const DLit &l, int j) {  // j = 1..
     return (uint32_t)(l.left >> (64 - 8 * j)) & 0xFFu;
 }
 
-// Constants of the SWAR compare against one literal byte c.
-struct ByteCmp {
-    uint32_t add;  // per byte 0x80 - (c & 0x7f): low-7-bit compare lands in bit 7
-    uint32_t sel;  // all ones if c < 0x80 (x >= c iff high bit or low bits >= c)
-    uint32_t rep;  // c in every byte
-};
+// threshold constants for "byte >= k", k in 0..256
+__device__ __forceinline__ uint32_t thr_add(uint32_t k) { return k >= 256u ? 0u : (0x80u - (k & 0x7Fu)) * 0x01010101u; }
+__device__ __forceinline__ bool thr_hi(uint32_t k) { return k >= 128u; }
 
-__device__ __forceinline__ ByteCmp make_cmp(uint32_t c) {
-    ByteCmp k;
-    k.add = (0x80u - (c & 0x7Fu)) * 0x01010101u;
-    k.sel = (c & 0x80u) ? 0u : kFull;
-    k.rep = c * 0x01010101u;
-    return k;
+template <bool HI>
+__device__ __forceinline__ uint32_t ge_msb(uint32_t x, uint32_t x7, uint32_t add) {
+    const uint32_t y = x7 + add;
+    return HI ? (y & x & kMsb) : ((y | x) & kMsb);
 }
 
-// Bit 7 of every byte: lt = (x_byte < c), eq = (x_byte == c), unsigned.
-__device__ __forceinline__ void cmp_word(uint32_t x, const ByteCmp &k, uint32_t &lt, uint32_t &eq) {
-    uint32_t y = (x & 0x7F7F7F7Fu) + k.add;
-    uint32_t ge = (y & x) | ((y | x) & k.sel);
-    lt = ~ge & 0x80808080u;
-    uint32_t t = x ^ k.rep;
-    uint32_t z = (t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;
-    eq = ~(z | t) & 0x80808080u;
+__device__ __forceinline__ uint32_t ge_msb_rt(uint32_t x, uint32_t x7, uint32_t add, uint32_t sel) {
+    const uint32_t y = x7 + add;
+    return ((y & x) | ((y | x) & sel)) & kMsb;
 }
 
 __device__ __forceinline__ uint32_t gather8(const uint32_t m[8]) {
     return (m[0] >> 7) | (m[1] >> 6) | (m[2] >> 5) | (m[3] >> 4) | (m[4] >> 3) | (m[5] >> 2) | (m[6] >> 1) | m[7];
 }
 
-__device__ __forceinline__ void cmp32(const uint32_t x[8], const ByteCmp &k, uint32_t &LT, uint32_t &EQ) {
-    uint32_t lt[8], eq[8];
+// Byte 1 against literal byte c with compile-time high bits of c and c + 1.
+// GE = rows with byte >= c; EQ = rows with byte == c (only if NEED_EQ).
+template <bool HI0, bool HI1, bool NEED_EQ>
+__device__ __forceinline__ void cmp32_fast(const uint32_t x[8], uint32_t add0, uint32_t add1, uint32_t &GE,
+                                           uint32_t &EQ) {
+    uint32_t ge[8], eq[8];
 #pragma unroll
-    for (int w = 0; w < 8; w++) cmp_word(x[w], k, lt[w], eq[w]);
-    LT = gather8(lt);
+    for (int w = 0; w < 8; w++) {
+        const uint32_t x7 = x[w] & kLow7;
+        ge[w] = ge_msb<HI0>(x[w], x7, add0);
+        if (NEED_EQ) eq[w] = ge[w] & ~ge_msb<HI1>(x[w], x7, add1);
+    }
+    GE = gather8(ge);
+    if (NEED_EQ) EQ = gather8(eq);
+}
+
+// Runtime-constant variant (deeper ByteSlice slices, BETWEEN's upper literal).
+__device__ __forceinline__ void cmp32_rt(const uint32_t x[8], uint32_t c, uint32_t &LT, uint32_t &EQ) {
+    const uint32_t a0 = thr_add(c), a1 = thr_add(c + 1);
+    const uint32_t s0 = thr_hi(c) ? 0u : kFull, s1 = thr_hi(c + 1) ? 0u : kFull;
+    uint32_t ge[8], eq[8];
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+        const uint32_t x7 = x[w] & kLow7;
+        ge[w] = ge_msb_rt(x[w], x7, a0, s0);
+        eq[w] = ge[w] & ~ge_msb_rt(x[w], x7, a1, s1);
+    }
+    LT = ~gather8(ge);
     EQ = gather8(eq);
 }
 
@@ -147,33 +182,34 @@ template <int NLIT>
 __device__ __noinline__ void vbs_deeper(const ScanK &a, uint32_t t, uint32_t lane, uint32_t &LT1, uint32_t &EQ1,
                                         uint32_t &LT2, uint32_t &EQ2) {
     const int K = a.K;
-    const int l1 = (int)a.lit[0].len;
-    const int l2 = NLIT == 2 ? (int)a.lit[1].len : 0;
-    bool done1 = false, done2 = (NLIT == 1);
-    const int jend = min(max(l1, l2) + 1, K);
+    const int l1 = (int)a.lit[0].len, e1 = a.lit[0].jend;
+    const int l2 = NLIT == 2 ? (int)a.lit[1].len : 0, e2 = NLIT == 2 ? a.lit[1].jend : 1;
+    const int jend = max(e1, e2);
     const uint64_t wbase = (uint64_t)t * kTileWords;
     for (int j = 2; j <= jend; j++) {
-        uint32_t pend = (done1 ? 0u : EQ1) | (done2 ? 0u : EQ2);
+        const bool act1 = j <= e1, act2 = NLIT == 2 && j <= e2;
+        const uint32_t pend = (act1 ? EQ1 : 0u) | (act2 ? EQ2 : 0u);
         if (!__any_sync(kFull, pend != 0u)) break;
         // M_j only for 256-row groups (8 lanes) holding a pending row
-        uint32_t bal = __ballot_sync(kFull, pend != 0u);
-        uint32_t gact = (bal >> (lane & 24u)) & 0xFFu;
-        uint32_t mj = gact ? __ldg(a.mask[j] + wbase + lane) : 0u;
-        if (!done1) {
+        const uint32_t bal = __ballot_sync(kFull, pend != 0u);
+        const uint32_t gact = (bal >> (lane & 24u)) & 0xFFu;
+        const uint32_t mj = gact ? __ldg(a.mask[j] + wbase + lane) : 0u;
+        if (act1) {
             if (j <= l1) { LT1 |= EQ1 & ~mj; EQ1 &= mj; }   // row ends first: smaller
-            else { EQ1 &= ~mj; done1 = true; }             // row continues: larger; else equal
+            else EQ1 &= ~mj;                               // row continues: larger; else equal
         }
-        if (NLIT == 2 && !done2) {
+        if (act2) {
             if (j <= l2) { LT2 |= EQ2 & ~mj; EQ2 &= mj; }
-            else { EQ2 &= ~mj; done2 = true; }
+            else EQ2 &= ~mj;
         }
-        uint32_t need = (done1 ? 0u : EQ1) | (done2 ? 0u : EQ2);
+        const uint32_t need = (act1 && j <= l1 ? EQ1 : 0u) | (act2 && j <= l2 ? EQ2 : 0u);
         if (!__any_sync(kFull, need != 0u)) continue;
         // rank of each byte in BS_j: exclusive prefix of popcounts inside the group
-        uint32_t cnt = __popc(mj), incl = cnt;
+        const uint32_t cnt = __popc(mj);
+        uint32_t incl = cnt;
 #pragma unroll
         for (int d = 1; d < 8; d <<= 1) {
-            uint32_t v = __shfl_up_sync(kFull, incl, d);
+            const uint32_t v = __shfl_up_sync(kFull, incl, d);
             if ((lane & 7u) >= (uint32_t)d) incl += v;
         }
         if (need) {
@@ -189,16 +225,13 @@ __device__ __noinline__ void vbs_deeper(const ScanK &a, uint32_t t, uint32_t lan
                 bits &= bits - 1;
                 const uint64_t idx = base + __popc(mj & (bit - 1u));
                 uint32_t byte = 0;
-                if (idx < dlen) {
-                    byte = __ldg(deep + idx);
-                } else {
-                    atomicOr(a.status, kStatusBounds);
-                }
-                if (!done1 && (EQ1 & bit)) {
+                if (idx < dlen) byte = __ldg(deep + idx);
+                else atomicOr(a.status, kStatusBounds);
+                if (act1 && j <= l1 && (EQ1 & bit)) {
                     if (byte < c1) { LT1 |= bit; EQ1 &= ~bit; }
                     else if (byte > c1) EQ1 &= ~bit;
                 }
-                if (NLIT == 2 && !done2 && (EQ2 & bit)) {
+                if (act2 && j <= l2 && (EQ2 & bit)) {
                     if (byte < c2) { LT2 |= bit; EQ2 &= ~bit; }
                     else if (byte > c2) EQ2 &= ~bit;
                 }
@@ -206,8 +239,8 @@ __device__ __noinline__ void vbs_deeper(const ScanK &a, uint32_t t, uint32_t lan
         }
     }
     // a literal longer than every stored code: an equal prefix means a shorter row
-    if (!done1 && l1 > K) { LT1 |= EQ1; EQ1 = 0; }
-    if (NLIT == 2 && !done2 && l2 > K) { LT2 |= EQ2; EQ2 = 0; }
+    if (l1 > K) { LT1 |= EQ1; EQ1 = 0; }
+    if (NLIT == 2 && l2 > K) { LT2 |= EQ2; EQ2 = 0; }
 }
 
 // ---------------------------------------------------- ByteSlice slices >= 2
@@ -221,11 +254,11 @@ __device__ __noinline__ void bsl_deeper(const ScanK &a, uint32_t t, uint32_t lan
             uint32_t x[8];
             load_lane32(a.dense + (uint64_t)(j - 1) * a.slice_bytes + (uint64_t)t * kTileRows, lane, x);
             uint32_t lt, eq;
-            cmp32(x, make_cmp(lit_byte(a.lit[0], j)), lt, eq);
+            cmp32_rt(x, lit_byte(a.lit[0], j), lt, eq);
             LT1 |= EQ1 & lt;
             EQ1 &= eq;
             if (NLIT == 2) {
-                cmp32(x, make_cmp(lit_byte(a.lit[1], j)), lt, eq);
+                cmp32_rt(x, lit_byte(a.lit[1], j), lt, eq);
                 LT2 |= EQ2 & lt;
                 EQ2 &= eq;
             }
@@ -233,36 +266,76 @@ __device__ __noinline__ void bsl_deeper(const ScanK &a, uint32_t t, uint32_t lan
     }
 }
 
-template <bool VBS, int NLIT>
-__global__ void __launch_bounds__(kScanThreads) scan_dense_kernel(const ScanK a) {
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    const ByteCmp k1 = make_cmp(lit_byte(a.lit[0], 1));
-    const ByteCmp k2 = make_cmp(lit_byte(a.lit[NLIT - 1], 1));
-    for (uint32_t t = gw; t < a.n_tiles; t += nw) {
-        const uint64_t w = (uint64_t)t * kTileWords + lane;
-        uint32_t sd = valid_mask(w * 32u, a.n);  // 0 for words at or past ceil(n/32)
-        if (a.seed && sd) sd &= __ldg(a.seed + w);
-        uint32_t LT1 = 0, EQ1 = 0, LT2 = 0, EQ2 = 0;
-        if (sd) {
-            uint32_t x[8];
-            load_lane32(a.dense + (uint64_t)t * kTileRows, lane, x);
-            cmp32(x, k1, LT1, EQ1);
-            LT1 &= sd;
-            EQ1 &= sd;
-            if (NLIT == 2) {
-                cmp32(x, k2, LT2, EQ2);
-                LT2 &= sd;
-                EQ2 &= sd;
-            }
-        }
-        if (a.has_deeper && __any_sync(kFull, (EQ1 | EQ2) != 0u)) {
+// One tile whose lane bytes are in x: byte 1, deeper levels, result word.
+template <bool VBS, int NLIT, bool HI0, bool HI1, bool NEED_EQ>
+__device__ __forceinline__ void scan_tile(const ScanK &a, uint32_t t, uint32_t lane, const uint32_t x[8],
+                                          uint32_t sd, uint32_t add0, uint32_t add1) {
+    uint32_t GE1, EQ1 = 0, LT2 = 0, EQ2 = 0;
+    cmp32_fast<HI0, HI1, NEED_EQ>(x, add0, add1, GE1, EQ1);
+    uint32_t LT1 = sd & ~GE1;
+    EQ1 &= sd;
+    if (NLIT == 2) {
+        cmp32_rt(x, lit_byte(a.lit[1], 1), LT2, EQ2);
+        LT2 &= sd;
+        EQ2 &= sd;
+    }
+    if (NEED_EQ || NLIT == 2) {
+        if (__any_sync(kFull, (EQ1 | EQ2) != 0u)) {
             if (VBS) vbs_deeper<NLIT>(a, t, lane, LT1, EQ1, LT2, EQ2);
             else bsl_deeper<NLIT>(a, t, lane, LT1, EQ1, LT2, EQ2);
         }
-        if (w * 32u < a.n) st_stream(a.out + w, final_bits(a.op, sd, LT1, EQ1, LT2, EQ2));
     }
+    const uint64_t w = (uint64_t)t * kTileWords + lane;
+    if (w * 32u < a.n) st_stream(a.out + w, final_bits(a.op, sd, LT1, EQ1, LT2, EQ2));
+}
+
+template <bool VBS, int NLIT, bool HI0, bool HI1, bool NEED_EQ>
+__global__ void __launch_bounds__(kScanThreads) scan_dense_kernel(const ScanK a) {
+    __shared__ __align__(16) uint8_t ring[kScanWarps][kStages][kTileRows];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t c0 = lit_byte(a.lit[0], 1);
+    const uint32_t add0 = thr_add(c0), add1 = thr_add(c0 + 1);
+
+    if (a.seed) {
+        // seeded: lanes whose seed word is zero read nothing
+        for (uint32_t t = gw; t < a.n_tiles; t += nw) {
+            const uint64_t w = (uint64_t)t * kTileWords + lane;
+            uint32_t sd = valid_mask(w * 32u, a.n);
+            if (sd) sd &= __ldg(a.seed + w);
+            uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (sd) load_lane32(a.dense + (uint64_t)t * kTileRows, lane, x);
+            scan_tile<VBS, NLIT, HI0, HI1, NEED_EQ>(a, t, lane, x, sd, add0, add1);
+        }
+        return;
+    }
+    // unseeded: 3-stage cp.async ring, two tiles in flight ahead of the one resolved
+    uint8_t *my = &ring[warp][0][0];
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(my);
+    auto issue = [&](uint32_t t, int stage) {
+        if (t < a.n_tiles) {
+            const uint8_t *g = a.dense + (uint64_t)t * kTileRows;
+            const uint32_t s = sbase + (uint32_t)stage * kTileRows;
+            cp_async16(s + lane * 16u, g + lane * 16u);
+            cp_async16(s + 512u + lane * 16u, g + 512u + lane * 16u);
+        }
+        cp_async_commit();  // empty groups keep the group count uniform
+    };
+    issue(gw, 0);
+    issue(gw + nw, 1);
+    int stage = 0;
+    for (uint32_t t = gw; t < a.n_tiles; t += nw) {
+        issue(t + 2 * nw, (stage + 2) % kStages);
+        cp_async_wait<kStages - 1>();
+        const uint4 *sp = reinterpret_cast<const uint4 *>(my + stage * kTileRows);
+        const uint4 v0 = sp[lane], v1 = sp[32 + lane];
+        const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        const uint32_t sd = valid_mask(((uint64_t)t * kTileWords + lane) * 32u, a.n);
+        scan_tile<VBS, NLIT, HI0, HI1, NEED_EQ>(a, t, lane, x, sd, add0, add1);
+        stage = (stage + 1) % kStages;
+    }
+    cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------ Bit-Packed
@@ -322,12 +395,28 @@ __global__ void scan_fill_kernel(const ScanK a) {
 }
 
 // ---------------------------------------------------------------- host side
-template <class F>
-int grid_for(F kernel, uint32_t n_tiles, int device) {
+using KernelFn = void (*)(const ScanK);
+
+int grid_for(KernelFn kernel, uint32_t n_tiles, int device) {
     const int per_sm = blocks_per_sm((const void *)kernel, kScanThreads, 0, device);
-    const uint64_t want = ((uint64_t)n_tiles + (kScanThreads / 32) - 1) / (kScanThreads / 32);
+    const uint64_t want = ((uint64_t)n_tiles + kScanWarps - 1) / kScanWarps;
     const uint64_t cap = (uint64_t)sm_count(device) * (uint64_t)per_sm;
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, cap));
+}
+
+template <bool VBS, int NLIT>
+KernelFn pick_dense(bool hi0, bool hi1, bool need_eq) {
+    const int sel = (hi0 ? 4 : 0) | (hi1 ? 2 : 0) | (need_eq ? 1 : 0);
+    switch (sel) {
+    case 0: return scan_dense_kernel<VBS, NLIT, false, false, false>;
+    case 1: return scan_dense_kernel<VBS, NLIT, false, false, true>;
+    case 2: return scan_dense_kernel<VBS, NLIT, false, true, false>;
+    case 3: return scan_dense_kernel<VBS, NLIT, false, true, true>;
+    case 4: return scan_dense_kernel<VBS, NLIT, true, false, false>;
+    case 5: return scan_dense_kernel<VBS, NLIT, true, false, true>;
+    case 6: return scan_dense_kernel<VBS, NLIT, true, true, false>;
+    default: return scan_dense_kernel<VBS, NLIT, true, true, true>;
+    }
 }
 
 DLit make_dlit(const LitCode &l) {
@@ -353,8 +442,8 @@ int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_
     a.op = p.op;
     if (p.mode != Pred::kNormal) {
         a.fill_all = p.mode == Pred::kAll;
-        uint64_t nwords = (uint64_t)c.n_tiles * kTileWords;
-        int grid = (int)std::min<uint64_t>((nwords + 255) / 256, (uint64_t)sm_count(dev) * 8);
+        const uint64_t nwords = (c.n + 31) / 32;
+        const int grid = (int)std::min<uint64_t>((nwords + 255) / 256, (uint64_t)sm_count(dev) * 8);
         scan_fill_kernel<<<std::max(grid, 1), 256, 0, s>>>(a);
         return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
     }
@@ -377,13 +466,13 @@ int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_
         case BS_NE: a.lo = c1; a.hi = c1; a.invert = 1; break;
         default: a.lo = c1; a.hi = c2; break;
         }
-        int grid = grid_for(scan_packed_kernel, c.n_tiles, dev);
-        scan_packed_kernel<<<grid, kScanThreads, 0, s>>>(a);
+        scan_packed_kernel<<<grid_for(scan_packed_kernel, c.n_tiles, dev), kScanThreads, 0, s>>>(a);
         return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
     }
     a.dense = c.d_dense;
     a.slice_bytes = c.dense_slice_bytes();
     LitCode l0 = p.lit[0], l1 = nlit == 2 ? p.lit[1] : p.lit[0];
+    const int K = c.layout == BS_PPVBS ? c.K : c.S;
     if (c.layout == BS_BYTESLICE) {
         // ByteSlice bytes are those of the code left-aligned in S bytes
         l0.code <<= (8 * c.S - c.k);
@@ -392,30 +481,30 @@ int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_
     }
     a.lit[0] = make_dlit(l0);
     a.lit[1] = make_dlit(l1);
+    a.K = K;
+    // does the result depend on "equal after the literal's last byte"?
+    const bool need_eq0 = !(p.op == BS_LT || p.op == BS_GE || p.op == BS_BETWEEN);
+    a.lit[0].jend = need_eq0 ? std::min((int)l0.len + 1, K) : std::min((int)l0.len, K);
+    a.lit[1].jend = nlit == 2 ? std::min((int)l1.len + 1, K) : 1;  // BETWEEN's upper end: v <= c2
+    // the EQ mask of byte 1 matters if a deeper level can still decide
+    // "smaller", or if the predicate reads it directly
+    const bool eq_at_1 = need_eq0 || l0.len >= 2;
     if (c.layout == BS_PPVBS) {
-        a.K = c.K;
         for (int j = 2; j <= c.K; j++) {
             a.mask[j] = c.d_mask[j];
             a.off[j] = c.d_off[j];
             a.deep[j] = c.d_deep[j];
             a.deep_len[j] = c.deep_len[j];
         }
-        int lmax = (int)std::max(a.lit[0].len, a.lit[1].len);
-        a.has_deeper = (c.K >= 2 || lmax >= 2) ? 1 : 0;
-        if (nlit == 2) {
-            scan_dense_kernel<true, 2><<<grid_for(scan_dense_kernel<true, 2>, c.n_tiles, dev), kScanThreads, 0, s>>>(a);
-        } else {
-            scan_dense_kernel<true, 1><<<grid_for(scan_dense_kernel<true, 1>, c.n_tiles, dev), kScanThreads, 0, s>>>(a);
-        }
-    } else {
-        a.K = c.S;
-        a.has_deeper = c.S >= 2 ? 1 : 0;
-        if (nlit == 2) {
-            scan_dense_kernel<false, 2><<<grid_for(scan_dense_kernel<false, 2>, c.n_tiles, dev), kScanThreads, 0, s>>>(a);
-        } else {
-            scan_dense_kernel<false, 1><<<grid_for(scan_dense_kernel<false, 1>, c.n_tiles, dev), kScanThreads, 0, s>>>(a);
-        }
     }
+    const uint32_t cb = (uint32_t)(a.lit[0].left >> 56);
+    const bool hi0 = cb >= 128u, hi1 = cb + 1 >= 128u;
+    KernelFn fn;
+    if (c.layout == BS_PPVBS)
+        fn = nlit == 2 ? pick_dense<true, 2>(hi0, hi1, true) : pick_dense<true, 1>(hi0, hi1, eq_at_1);
+    else
+        fn = nlit == 2 ? pick_dense<false, 2>(hi0, hi1, true) : pick_dense<false, 1>(hi0, hi1, eq_at_1);
+    fn<<<grid_for(fn, c.n_tiles, dev), kScanThreads, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
 
