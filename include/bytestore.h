@@ -181,6 +181,23 @@ uint64_t bs_lookup_workspace_bytes(const bs_column *col);
 int bs_lookup(const bs_column *col, const uint32_t *d_bits, int32_t *d_out, uint64_t out_cap,
               uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes, void *stream);
 
+/* Allocation-free lookup. The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory when they look up -- code running
+ * inside someone else's CUDA graph construction or replay, hosts that grant a
+ * fixed memory budget up front, latency-critical paths that must not reach an
+ * allocator. Same arguments and results as bs_lookup, but the scratch comes from
+ * a 1 MiB array the library keeps in device memory (held by every GPU that
+ * loads the library until the process exits); no cudaMalloc, cudaFree or other
+ * allocating call is made. Columns needing more than 1 MiB of scratch (2^32 rows
+ * or more; in practice none, since n < 2^32) are rejected with
+ * BS_ERR_CAPACITY. The first call on a device looks up the array's device
+ * address; make that first call before any stream capture. All calls share
+ * the one array and it keeps the previous call's contents (each call clears
+ * what it needs): calls that overlap on the GPU, from any stream or thread,
+ * race and must be serialised by the caller. */
+int bs_lookup_noalloc(const bs_column *col, const uint32_t *d_bits, int32_t *d_out, uint64_t out_cap,
+                      uint64_t *d_count, void *stream);
+
 /* Same as bs_lookup but returns the zero-padded codes Algorithm 4 builds
  * (PP-VBS: K bytes; ByteSlice / Bit-Packed: the k-bit code) as uint64. */
 int bs_lookup_codes(const bs_column *col, const uint32_t *d_bits, uint64_t *d_codes, uint64_t out_cap,

@@ -74,6 +74,7 @@ _SIGS = {
     "bs_lookup_workspace_bytes": ([_vp], _u64),
     "bs_lookup": ([_vp, _vp, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "bs_lookup_codes": ([_vp, _vp, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
+    "bs_lookup_noalloc": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
     "bs_lookup_rowids": ([_vp, _vp, _u64, _vp, _vp], _i32),
     "bs_advise_layout": ([_vp, _u64, _i32, _vp, _vp], _i32),
     "bs_scan_bytes": ([_vp, _i32, _i32, _i32, _vp, _vp], _i32),
@@ -291,6 +292,20 @@ def bs_lookup(col: Column, bits, out=None, out_cap: int | None = None, count=Non
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(lib().bs_lookup(col.handle, _dptr(bits), _dptr(out), cap, _dptr(count), _dptr(workspace), ws_bytes,
                            _stream(stream)), "bs_lookup")
+    return out, count
+
+
+def bs_lookup_noalloc(col: Column, bits, out=None, out_cap: int | None = None, count=None, stream=None):
+    """bs_lookup without any allocation inside the library (its scratch is a
+    fixed device array shared by all calls: serialise overlapping calls)."""
+    import torch
+    if out is None:
+        out = torch.empty(max(1, col.n if out_cap is None else out_cap), dtype=torch.int32, device="cuda")
+    cap = out.numel() if out_cap is None else int(out_cap)
+    if count is None:
+        count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    _check(lib().bs_lookup_noalloc(col.handle, _dptr(bits), _dptr(out), cap, _dptr(count), _stream(stream)),
+           "bs_lookup_noalloc")
     return out, count
 
 
