@@ -186,11 +186,11 @@ int bs_lookup(const bs_column *col, const uint32_t *d_bits, int32_t *d_out, uint
  * inside someone else's CUDA graph construction or replay, hosts that grant a
  * fixed memory budget up front, latency-critical paths that must not reach an
  * allocator. Same arguments and results as bs_lookup, but the scratch comes from
- * a 1 MiB array the library keeps in device memory (held by every GPU that
+ * a 2 MiB + 4 KiB array the library keeps in device memory (held by every GPU that
  * loads the library until the process exits); no cudaMalloc, cudaFree or other
- * allocating call is made. Columns needing more than 1 MiB of scratch (2^32 rows
- * or more; in practice none, since n < 2^32) are rejected with
- * BS_ERR_CAPACITY. The first call on a device looks up the array's device
+ * allocating call is made. Columns needing more than that scratch (2 MiB +
+ * 4 KiB: 2^32 rows or more; in practice none, since n < 2^32) are rejected
+ * with BS_ERR_CAPACITY. The first call on a device looks up the array's device
  * address; make that first call before any stream capture. All calls share
  * the one array and it keeps the previous call's contents (each call clears
  * what it needs): calls that overlap on the GPU, from any stream or thread,

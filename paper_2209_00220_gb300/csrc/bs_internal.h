@@ -35,8 +35,6 @@ constexpr int kGroupRows = 256;
 constexpr int kGroupWords = 8;
 constexpr int kGroupsPerTile = 4;
 constexpr int kMaxCodeBytes = 8;     // raw-code columns; Algorithm 1 yields <= 6
-constexpr int kTrieNodeWords = 512;  // 256 slot entries + 256 child entries
-constexpr uint32_t kTrieInternal = 0x80000000u;
 
 // Byte offset, inside its tile, of the byte of tile-local row q (0..1023).
 inline uint32_t tile_byte_pos(uint32_t q) {
@@ -77,8 +75,9 @@ struct Column {
     std::vector<uint64_t> dcode;  // PP-VBS: code of dict[i] (unpadded)
     std::vector<uint8_t> dlen;    // PP-VBS: its length in bytes
     std::vector<uint64_t> dcount; // rows holding dict[i] (observed dictionaries)
-    bool root_leaf = true;        // PP-VBS decode: the root node is a leaf
-    std::vector<uint32_t> trie;   // PP-VBS decode tables, kTrieNodeWords per internal node
+    std::vector<uint64_t> first_byte_rows;  // PP-VBS: rows whose code starts with byte b
+    std::vector<int32_t> val2;    // PP-VBS decode: value of codes <= 2 bytes, by first two bytes
+    std::vector<uint32_t> leaf2;  // PP-VBS decode: first dictionary index of a level-2 leaf
 
     // host copy of the device layout (kept for host_only / keep_host)
     bool has_host = false;
@@ -98,7 +97,8 @@ struct Column {
     const uint32_t *d_off[kMaxCodeBytes + 1] = {nullptr};
     const uint8_t *d_deep[kMaxCodeBytes + 1] = {nullptr};
     const uint32_t *d_packed = nullptr;
-    const uint32_t *d_trie = nullptr;
+    const int32_t *d_val2 = nullptr;
+    const uint32_t *d_leaf2 = nullptr;
     const int32_t *d_dict = nullptr;
     uint64_t dict_size() const { return dict.size(); }
     uint64_t dense_slice_bytes() const { return (uint64_t)n_tiles * kTileRows; }

@@ -162,13 +162,11 @@ static int build_dictionary(const int32_t *v, uint64_t n, int threads, std::vect
 // ---------------------------------------------------------- Algorithm 1
 // Codes are built top-down: every node knows the pointer path (prefix) that
 // leads to it, so a value's code is prefix . slot (internal node) or prefix .
-// beta-byte leaf number. The decode trie records, per internal node and byte,
-// the dictionary index of each slot and the target of each pointer.
+// beta-byte leaf number.
 namespace {
 struct PpeOut {
     std::vector<uint64_t> &C;
     std::vector<uint8_t> &L;
-    std::vector<uint32_t> &trie;
 };
 
 inline bool heavier(const std::vector<uint64_t> &Q, uint64_t a, uint64_t b) {
@@ -226,31 +224,22 @@ std::vector<uint64_t> top255(const std::vector<uint64_t> &Q, uint64_t s, uint64_
     return all;
 }
 
-// Encode an internal node over [s, e) at level b with pointer path `prefix`,
-// stored as trie node `node`. Children that are internal are appended to
-// `pending` (b + 1 < 2 only at the root).
-struct Pending { int b; uint64_t s, e, prefix; uint32_t node; };
+// Encode an internal node over [s, e) at level b with pointer path `prefix`.
+// Children that are internal are appended to `pending` (b + 1 < 2 only at the
+// root).
+struct Pending { int b; uint64_t s, e, prefix; };
 
 void internal_node(PpeOut &o, const std::vector<uint64_t> &Q, int b, uint64_t s, uint64_t e, uint64_t prefix,
-                   uint32_t node, std::vector<Pending> &pending, uint32_t &next_node, int threads) {
+                   std::vector<Pending> &pending, int threads) {
     std::vector<uint64_t> I = top255(Q, s, e, threads);
-    uint32_t *slot = &o.trie[(size_t)node * kTrieNodeWords];
-    uint32_t *child = slot + 256;
     for (int t = 0; t < 255; t++) {
         o.C[I[t]] = (prefix << 8) | (uint64_t)(t + 1);
         o.L[I[t]] = (uint8_t)(b + 1);
-        slot[t + 1] = (uint32_t)I[t];
     }
     auto sub = [&](uint32_t ptr, uint64_t cs, uint64_t ce) {
         uint64_t cp = (prefix << 8) | ptr;
-        if (ce - cs < 256 || b + 1 >= 2) {
-            leaf(o, b + 1, cs, ce, cp);
-            child[ptr] = (uint32_t)cs;
-        } else {
-            uint32_t id = next_node++;
-            child[ptr] = kTrieInternal | id;
-            pending.push_back({b + 1, cs, ce, cp, id});
-        }
+        if (ce - cs < 256 || b + 1 >= 2) leaf(o, b + 1, cs, ce, cp);
+        else pending.push_back({b + 1, cs, ce, cp});
     };
     sub(0, s, I[0]);
     for (int t = 0; t < 254; t++) sub((uint32_t)(t + 1), I[t] + 1, I[t + 1]);
@@ -259,25 +248,17 @@ void internal_node(PpeOut &o, const std::vector<uint64_t> &Q, int b, uint64_t s,
 }  // namespace
 
 static void ppe_numerical(const std::vector<uint64_t> &Q, std::vector<uint64_t> &C, std::vector<uint8_t> &L,
-                          std::vector<uint32_t> &trie, bool &root_leaf, int threads) {
+                          int threads) {
     uint64_t nd = Q.size();
     C.assign(nd, 0);
     L.assign(nd, 0);
-    trie.clear();
+    PpeOut o{C, L};
     if (nd < 256) {
-        root_leaf = true;
-        std::vector<uint32_t> dummy;
-        PpeOut o{C, L, dummy};
         leaf(o, 0, 0, nd, 0);
         return;
     }
-    root_leaf = false;
-    // root + at most 256 level-1 internal nodes
-    trie.assign((size_t)257 * kTrieNodeWords, 0);
-    PpeOut o{C, L, trie};
     std::vector<Pending> level1;
-    uint32_t next_node = 1;
-    internal_node(o, Q, 0, 0, nd, 0, 0, level1, next_node, threads);
+    internal_node(o, Q, 0, 0, nd, 0, level1, threads);
     // level-1 internal nodes are independent: encode them in parallel
     std::vector<std::vector<Pending>> none(level1.size());
     std::atomic<size_t> cursor{0};
@@ -286,14 +267,36 @@ static void ppe_numerical(const std::vector<uint64_t> &Q, std::vector<uint64_t> 
     for (int t = 0; t < T; t++) {
         th.emplace_back([&] {
             for (size_t i; (i = cursor.fetch_add(1)) < level1.size();) {
-                uint32_t dummy = 0;
                 const Pending &p = level1[i];
-                internal_node(o, Q, p.b, p.s, p.e, p.prefix, p.node, none[i], dummy, 1);
+                internal_node(o, Q, p.b, p.s, p.e, p.prefix, none[i], 1);
             }
         });
     }
     for (auto &x : th) x.join();
-    trie.resize((size_t)next_node * kTrieNodeWords);
+}
+
+// Lookup decode tables for PP-VBS, indexed by the first two code bytes
+// (c1 << 8 | c2, with c2 = 0 for one-byte codes): val2 holds the value of every
+// code of at most two bytes; for longer codes -- which all sit in level-2 leaves
+// whose values have consecutive dictionary indices and codes 1, 2, ... after
+// the two-byte pointer path -- leaf2 holds the dictionary index of the leaf's
+// first value, so value = dict[leaf2[c1 c2] + rest - 1].
+static void build_decode_tables(Column &c) {
+    c.val2.assign(65536, 0);
+    c.leaf2.assign(65536, 0);
+    for (size_t i = 0; i < c.dict.size(); i++) {
+        const uint64_t C = c.dcode[i];
+        const int L = c.dlen[i];
+        if (L == 1) {
+            c.val2[(size_t)(C << 8)] = c.dict[i];
+        } else if (L == 2) {
+            c.val2[(size_t)C] = c.dict[i];
+        } else {
+            const uint64_t key = C >> (8 * (L - 2));
+            const uint64_t rest = C & ((1ull << (8 * (L - 2))) - 1);
+            c.leaf2[(size_t)key] = (uint32_t)(i - (rest - 1));
+        }
+    }
 }
 
 // ------------------------------------------------------------- layouts
@@ -431,8 +434,12 @@ int encode_values(const int32_t *values, uint64_t n, bs_layout layout, const bs_
             std::vector<uint32_t> ridx;
             int rc = build_dictionary(values, n, T, c.dict, Q, ridx);
             if (rc) return rc;
-            ppe_numerical(Q, c.dcode, c.dlen, c.trie, c.root_leaf, T);
+            ppe_numerical(Q, c.dcode, c.dlen, T);
             c.dcount = Q;
+            build_decode_tables(c);
+            c.first_byte_rows.assign(256, 0);
+            for (size_t i = 0; i < Q.size(); i++)
+                c.first_byte_rows[(size_t)((c.dcode[i] >> (8 * (c.dlen[i] - 1))) & 0xFF)] += Q[i];
             c.K = 1;
             for (uint8_t l : c.dlen) c.K = std::max<int>(c.K, l);
             const uint64_t *dc = c.dcode.data();

@@ -3,21 +3,29 @@
 // order, or zero-padded codes.
 //
 // Algorithm 4 walks the bit vector word by word with running slice indices
-// I_j; on the GPU the output position of every selected row comes from a
-// three-kernel compaction instead:
-//   1. count:   popcount of the bit vector per chunk of 16 tiles (16K rows);
-//   2. offsets: one CTA turns the chunk counts into exclusive offsets and
-//               writes the total;
-//   3. gather:  per tile, a warp prefix-sums its 32 word popcounts, lists the
-//               selected rows in shared memory (ascending), then lanes take
-//               list entries round-robin, so output writes are coalesced.
+// I_j. On the GPU the output position of every selected row comes from three
+// kernels instead:
+//   1. count:  one warp per chunk of 16 tiles (16K rows) popcounts its 2 KB of
+//              the bit vector with 16-byte loads; each CTA (8 chunks) also
+//              writes the total of its 8 chunks;
+//   2. scan:   one CTA turns the CTA totals into exclusive offsets (coalesced
+//              segments of 4096) and writes the selected-row count;
+//   3. gather: one CTA per chunk; its offset is its CTA offset plus the counts
+//              of the chunks before it in the same group of 8. Per tile, a warp
+//              prefix-sums its 32 word popcounts, lists the selected rows in
+//              shared memory (ascending), and lanes take list entries
+//              round-robin, four at a time, so output writes are coalesced and
+//              many loads are in flight.
+//
 // For PP-VBS a warp loads, per level j, the mask words M_j of the 256-row
-// groups whose selected rows have byte j-1 (the paper's per-block beta test),
-// prefix-sums their popcounts into shared memory, and every selected row then
-// finds its byte j at off_j[group] + prefix + rank. The code is decoded with the
-// prefix-preserving tree: root and level-1 internal nodes map a slot sub-code
-// to the dictionary index, a pointer sub-code to a child node or to a leaf
-// whose values have consecutive dictionary indices.
+// groups whose selected rows have byte j-1 (the paper's per-block beta test)
+// and prefix-sums their popcounts into shared memory; a selected row's length
+// and the address of each of its bytes then come from shared memory alone, so
+// all its byte loads are issued together. A tile with many selected rows first
+// copies its 1 KB of BS_1 into shared memory with coalesced 16-byte loads.
+// Codes of at most two bytes decode with one table load (value by first two
+// bytes); longer codes sit in level-2 leaves whose values have consecutive
+// dictionary indices, decoded as dict[leaf start + rest - 1].
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,7 +40,11 @@ constexpr int kChunkTiles = 16;
 constexpr int kLookupThreads = 256;
 constexpr int kLookupWarps = kLookupThreads / 32;
 constexpr int kTilesPerWarp = kChunkTiles / kLookupWarps;
+constexpr int kUnroll = 4;
+constexpr int kGroupChunks = 8;       // chunks counted by one CTA of the count kernel
 constexpr int kScanBlock = 1024;
+constexpr uint32_t kStageMin = 64;    // selected rows from which a tile stages BS_1
+constexpr uint32_t kSparseMax = 256;  // selected rows up to which a chunk is resolved row-parallel
 
 struct LookK {
     int32_t layout;
@@ -40,8 +52,6 @@ struct LookK {
     int32_t k;            // code bits (ByteSlice / Bit-Packed)
     int32_t identity;
     int64_t domain_min;
-    int32_t root_leaf;
-    uint32_t n_trie_nodes;
     uint64_t n;
     uint32_t n_tiles;
     uint32_t n_chunks;
@@ -52,11 +62,15 @@ struct LookK {
     const uint8_t *deep[kMaxCodeBytes + 1];
     uint64_t deep_len[kMaxCodeBytes + 1];
     const uint32_t *packed;
-    const uint32_t *trie;
+    const int32_t *val2;
+    const uint32_t *leaf2;
     const int32_t *dict;
     uint64_t dict_size;
     const uint32_t *bits;
-    uint32_t *chunk;      // workspace: chunk counts, then exclusive offsets
+    int32_t bits_vec;     // bits is 16-byte aligned
+    uint32_t n_groups;    // groups of kGroupChunks chunks
+    uint32_t *chunk_cnt;  // workspace: count per chunk
+    uint64_t *group_off;  // workspace: total per group, then exclusive offset
     int32_t *out_vals;
     uint64_t *out_codes;
     uint64_t out_cap;
@@ -75,90 +89,41 @@ __device__ __forceinline__ uint32_t tile_pos(uint32_t q) {
     return (w >> 2) * 512u + lane * 16u + (w & 3u) * 4u + b;
 }
 
+// A lane's 32 slice bytes arrive as words x0..x7 with word w byte b = row
+// 8b + w; two 4x4 byte transposes put them in row order (word k = rows
+// 4k..4k+3): rows 8m..8m+3 are byte m of x0..x3, rows 8m+4..8m+7 byte m of
+// x4..x7.
+__device__ __forceinline__ void transpose4(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t &y0,
+                                           uint32_t &y1, uint32_t &y2, uint32_t &y3) {
+    const uint32_t t0 = __byte_perm(a, b, 0x5140), t1 = __byte_perm(a, b, 0x7362);
+    const uint32_t t2 = __byte_perm(c, d, 0x5140), t3 = __byte_perm(c, d, 0x7362);
+    y0 = __byte_perm(t0, t2, 0x5410);
+    y1 = __byte_perm(t0, t2, 0x7632);
+    y2 = __byte_perm(t1, t3, 0x5410);
+    y3 = __byte_perm(t1, t3, 0x7632);
+}
+
+__device__ __forceinline__ void transpose_lane_bytes(const uint4 &v0, const uint4 &v1, uint4 &r0, uint4 &r1) {
+    uint32_t e0, e1, e2, e3, o0, o1, o2, o3;  // even / odd row-order words
+    transpose4(v0.x, v0.y, v0.z, v0.w, e0, e1, e2, e3);
+    transpose4(v1.x, v1.y, v1.z, v1.w, o0, o1, o2, o3);
+    r0 = make_uint4(e0, o0, e1, o1);
+    r1 = make_uint4(e2, o2, e3, o3);
+}
+
 __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
     return v;
 }
 
-// ------------------------------------------------------------ 1. count
-__global__ void __launch_bounds__(kLookupThreads) lookup_count_kernel(const LookK a) {
-    __shared__ uint32_t part[kLookupWarps];
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t chunk = blockIdx.x;
-    uint32_t acc = 0;
-    for (int i = 0; i < kTilesPerWarp; i++) {
-        const uint64_t t = (uint64_t)chunk * kChunkTiles + warp * kTilesPerWarp + i;
-        if (t < a.n_tiles) {
-            const uint64_t w = t * kTileWords + lane;
-            const uint32_t vm = valid_mask(w * 32u, a.n);  // never read past ceil(n/32) words
-            if (vm) acc += __popc(__ldg(a.bits + w) & vm);
-        }
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) part[warp] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t s = 0;
-        for (int i = 0; i < kLookupWarps; i++) s += part[i];
-        a.chunk[chunk] = s;
-    }
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+    return v;
 }
 
-// ------------------------------------------------------------ 2. offsets
-__global__ void __launch_bounds__(kScanBlock) lookup_offsets_kernel(const LookK a) {
-    __shared__ uint64_t sums[kScanBlock];
-    const uint32_t tid = threadIdx.x;
-    const uint32_t per = (a.n_chunks + kScanBlock - 1) / kScanBlock;
-    const uint64_t b = (uint64_t)tid * per, e = (b + per < a.n_chunks) ? b + per : (uint64_t)a.n_chunks;
-    uint64_t s = 0;
-    for (uint64_t i = b; i < e; i++) s += a.chunk[i];
-    sums[tid] = s;
-    __syncthreads();
-    // inclusive Hillis-Steele scan over the per-thread sums
-    for (uint32_t d = 1; d < kScanBlock; d <<= 1) {
-        uint64_t v = tid >= d ? sums[tid - d] : 0;
-        __syncthreads();
-        sums[tid] += v;
-        __syncthreads();
-    }
-    uint64_t run = tid ? sums[tid - 1] : 0;
-    for (uint64_t i = b; i < e; i++) {
-        uint32_t c = a.chunk[i];
-        a.chunk[i] = (uint32_t)run;
-        run += c;
-    }
-    if (tid == kScanBlock - 1 && a.count) *a.count = sums[kScanBlock - 1];
-}
-
-// ------------------------------------------------------------ 3. gather
-__device__ __forceinline__ int32_t decode_value(const LookK &a, uint64_t code, int len) {
-    uint64_t idx;
-    if (a.layout != BS_PPVBS) {
-        if (a.identity) return (int32_t)((int64_t)code + a.domain_min);
-        idx = code;
-    } else if (a.root_leaf) {
-        idx = code - 1;
-    } else {
-        uint32_t node = 0;
-        int pos = 0;
-        idx = ~0ull;
-        for (int guard = 0; guard < kMaxCodeBytes; guard++) {
-            const uint32_t b = (uint32_t)(code >> (8 * (len - 1 - pos))) & 0xFFu;
-            const uint32_t *nd = a.trie + (uint64_t)node * kTrieNodeWords;
-            if (pos == len - 1) { idx = __ldg(nd + b); break; }
-            const uint32_t ch = __ldg(nd + 256 + b);
-            pos++;
-            if (ch & kTrieInternal) {
-                node = ch & ~kTrieInternal;
-                if (node >= a.n_trie_nodes) break;
-                continue;
-            }
-            const uint64_t rest = code & ((8 * (len - pos) >= 64) ? ~0ull : ((1ull << (8 * (len - pos))) - 1));
-            idx = (uint64_t)ch + rest - 1;
-            break;
-        }
-    }
+__device__ __forceinline__ int32_t dict_value(const LookK &a, uint64_t idx) {
     if (idx >= a.dict_size) {
         atomicOr(a.status, kStatusBounds);
         return 0;
@@ -166,28 +131,165 @@ __device__ __forceinline__ int32_t decode_value(const LookK &a, uint64_t code, i
     return __ldg(a.dict + idx);
 }
 
-struct WarpSmem {
-    uint16_t list[kTileRows];
-    uint32_t mask[kMaxCodeBytes + 1][kTileWords];
-    uint32_t pref[kMaxCodeBytes + 1][kTileWords];
+// Value of a code: PP-VBS via the two-byte tables, the others by rank or range.
+template <int LAYOUT>
+__device__ __forceinline__ int32_t decode_value(const LookK &a, uint64_t code, int len) {
+    if (LAYOUT == BS_PPVBS) {
+        const uint32_t c1 = (uint32_t)(code >> (8 * (len - 1))) & 0xFFu;
+        const uint32_t c2 = len >= 2 ? (uint32_t)(code >> (8 * (len - 2))) & 0xFFu : 0u;
+        const uint32_t key = (c1 << 8) | c2;
+        if (len <= 2) return __ldg(a.val2 + key);
+        const uint64_t rest = code & ((1ull << (8 * (len - 2))) - 1);
+        return dict_value(a, (uint64_t)__ldg(a.leaf2 + key) + rest - 1);
+    }
+    if (a.identity) return (int32_t)((int64_t)code + a.domain_min);
+    return dict_value(a, code);
+}
+
+// 16-byte aligned: dense[] receives 16-byte vector stores, one struct per warp
+template <int KMAX>
+struct __align__(16) WarpSmemT {
+    uint8_t dense[kTileRows];         // staged BS_1 of the tile
+    uint32_t seg[KMAX <= 4 ? kTileRows / 4 + 4 : 4];  // staged BS_2 segment (dense path, KMAX <= 4)
+    uint16_t list[kTileRows];         // sparse path: selected rows; dense path: decode keys
+    uint32_t skip[kTileWords];        // dense path: entries already written
+    uint32_t mask[KMAX + 1][kTileWords];
+    uint32_t pref[KMAX + 1][kTileWords];
 };
 
-template <int LAYOUT, bool CODES>
-__device__ __forceinline__ void gather_tile(const LookK &a, uint64_t t, uint64_t out_base, WarpSmem &sm,
-                                            uint32_t lane) {
-    const uint64_t w = t * kTileWords + lane;
-    const uint32_t vm = valid_mask(w * 32u, a.n);
-    const uint32_t sel = vm ? (__ldg(a.bits + w) & vm) : 0u;
+static_assert(sizeof(WarpSmemT<2>) % 16 == 0 && sizeof(WarpSmemT<4>) % 16 == 0 && sizeof(WarpSmemT<8>) % 16 == 0,
+              "per-warp shared memory must keep 16-byte alignment");
+
+// Code (unpadded) and length of tile-local row q of tile t. PP-VBS reads the
+// warp's per-level mask words and BS_j prefixes from sm, and BS_1 from sm.dense
+// when the tile was staged. KMAX bounds the code length (template constant).
+template <int LAYOUT, int KMAX>
+__device__ __forceinline__ void fetch_code(const LookK &a, uint64_t t, uint32_t q, int levels,
+                                           const WarpSmemT<KMAX> *sm,
+                                           bool staged, uint64_t &code, int &len) {
+    if (LAYOUT == BS_PPVBS) {
+        const uint32_t wq = q >> 5, bq = q & 31u, below = (1u << bq) - 1u;
+        len = 1;
+#pragma unroll
+        for (int j = 2; j <= KMAX; j++)
+            if (j <= levels && len == j - 1 && ((sm->mask[j][wq] >> bq) & 1u)) len = j;
+        uint32_t b[KMAX + 1];
+        b[1] = staged ? (uint32_t)sm->dense[q] : (uint32_t)__ldg(a.dense + t * kTileRows + tile_pos(q));
+#pragma unroll
+        for (int j = 2; j <= KMAX; j++) {
+            b[j] = 0;
+            if (j <= len) {
+                const uint64_t idx = (uint64_t)sm->pref[j][wq] + __popc(sm->mask[j][wq] & below);
+                if (idx < a.deep_len[j]) b[j] = __ldg(a.deep[j] + idx);
+                else atomicOr(a.status, kStatusBounds);
+            }
+        }
+        code = b[1];
+#pragma unroll
+        for (int j = 2; j <= KMAX; j++)
+            if (j <= len) code = (code << 8) | b[j];
+    } else if (LAYOUT == BS_BYTESLICE) {
+        const uint64_t pos = t * kTileRows + tile_pos(q);
+        uint32_t b[KMAX];
+#pragma unroll
+        for (int s = 0; s < KMAX; s++) b[s] = s < a.K ? __ldg(a.dense + (uint64_t)s * a.slice_bytes + pos) : 0u;
+        uint64_t aligned = 0;
+#pragma unroll
+        for (int s = 0; s < KMAX; s++)
+            if (s < a.K) aligned = (aligned << 8) | b[s];
+        code = aligned >> (8 * a.K - a.k);
+        len = a.K;
+    } else {
+        const uint64_t bit = (t * kTileRows + q) * (uint64_t)a.k;
+        const uint32_t *p = a.packed + (bit >> 5);
+        const uint32_t lo = __ldg(p), hi = __ldg(p + 1);
+        code = __funnelshift_r(lo, hi, (uint32_t)(bit & 31u)) & (a.k == 32 ? kFull : ((1u << a.k) - 1u));
+        len = (a.k + 7) / 8;
+    }
+}
+
+// Dense PP-VBS tile: BS_1 and the tile's BS_2 segment are staged in shared
+// memory; each lane walks its own selected rows in order and leaves a 16-bit
+// decode key (first two code bytes) per output slot, codes of three or more
+// bytes being decoded on the spot; the warp then decodes the keys and writes
+// the values with coalesced stores.
+template <int KMAX>
+__device__ __forceinline__ void gather_dense_vbs(const LookK &a, uint64_t t, uint32_t sel, uint32_t excl,
+                                                 uint32_t total, int levels, uint64_t out_base, WarpSmemT<KMAX> &sm,
+                                                 const int32_t *val1, uint32_t lane) {
+    uint32_t seg_lo = 0;
+    if (levels >= 2) {
+        // BS_2 bytes of this tile are contiguous: [off_2[first group], off_2[first group of next tile])
+        seg_lo = __ldg(a.off[2] + t * kGroupsPerTile);
+        const uint32_t seg_hi = __ldg(a.off[2] + t * kGroupsPerTile + kGroupsPerTile);
+        const uint32_t w0 = seg_lo >> 2, w1 = (seg_hi + 3) >> 2;
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(a.deep[2]);
+        constexpr uint32_t kSegWords = sizeof(sm.seg) / 4;
+        for (uint32_t i = lane; i < w1 - w0 && i < kSegWords; i += 32) sm.seg[i] = __ldg(src + w0 + i);
+    }
+    sm.skip[lane] = 0u;
+    __syncwarp();
+    const uint8_t *seg = reinterpret_cast<const uint8_t *>(sm.seg) + (seg_lo & 3u);
+    const uint32_t m2 = levels >= 2 ? sm.mask[2][lane] : 0u;
+    const uint32_t p2 = levels >= 2 ? sm.pref[2][lane] - seg_lo : 0u;
+    const uint32_t m3 = (KMAX >= 3 && levels >= 3) ? sm.mask[KMAX >= 3 ? 3 : 2][lane] : 0u;
+    uint32_t pos = excl, r = sel;
+    while (r) {
+        const uint32_t b = __ffs(r) - 1, below = (1u << b) - 1u;
+        r &= r - 1;
+        const uint32_t q = lane * 32u + b;
+        const uint32_t c1 = sm.dense[q];
+        uint32_t key = c1 << 8;
+        if ((m2 >> b) & 1u) {
+            key |= seg[p2 + __popc(m2 & below)];
+            if (KMAX >= 3 && ((m3 >> b) & 1u)) {  // three or more bytes: decode now
+                uint64_t code;
+                int len;
+                fetch_code<BS_PPVBS, KMAX>(a, t, q, levels, &sm, true, code, len);
+                const uint64_t o = out_base + pos;
+                if (o < a.out_cap) a.out_vals[o] = decode_value<BS_PPVBS>(a, code, len);
+                atomicOr(&sm.skip[pos >> 5], 1u << (pos & 31));
+            }
+        }
+        sm.list[pos++] = (uint16_t)key;
+    }
+    __syncwarp();
+    for (uint32_t i0 = 0; i0 < total; i0 += 32 * kUnroll) {
+        int32_t v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+            v[u] = 0;
+            if (i < total) {
+                const uint32_t key = sm.list[i];
+                v[u] = (key & 0xFFu) ? __ldg(a.val2 + key) : val1[key >> 8];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+            const uint64_t o = out_base + i;
+            if (i < total && o < a.out_cap && !((sm.skip[i >> 5] >> (i & 31)) & 1u)) a.out_vals[o] = v[u];
+        }
+    }
+    __syncwarp();
+}
+
+template <int LAYOUT, bool CODES, int KMAX>
+__device__ __forceinline__ void gather_tile(const LookK &a, uint64_t t, uint32_t sel, uint64_t out_base,
+                                            WarpSmemT<KMAX> &sm, const int32_t *val1, uint32_t lane) {
     const uint32_t cnt = __popc(sel);
     uint32_t incl = cnt;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        uint32_t v = __shfl_up_sync(kFull, incl, d);
+        const uint32_t v = __shfl_up_sync(kFull, incl, d);
         if (lane >= (uint32_t)d) incl += v;
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     if (total == 0) return;
-    {
+    constexpr bool kDenseOk = LAYOUT == BS_PPVBS && !CODES && KMAX <= 4;
+    const bool dense = kDenseOk && total >= kStageMin;
+    if (!dense) {
         uint32_t pos = incl - cnt, r = sel;
         while (r) {
             const uint32_t b = __ffs(r) - 1;
@@ -195,11 +297,23 @@ __device__ __forceinline__ void gather_tile(const LookK &a, uint64_t t, uint64_t
             sm.list[pos++] = (uint16_t)(lane * 32u + b);
         }
     }
+    // a dense tile copies its BS_1 bytes once, coalesced, instead of one load
+    // per row, and stores them in plain row order (byte of row q at dense[q])
+    const bool staged = LAYOUT == BS_PPVBS && total >= kStageMin;
+    if (staged) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.dense + t * kTileRows);
+        const uint4 v0 = __ldg(src + lane), v1 = __ldg(src + 32 + lane);
+        uint4 r0, r1;
+        transpose_lane_bytes(v0, v1, r0, r1);
+        uint4 *dst = reinterpret_cast<uint4 *>(sm.dense + lane * 32u);
+        dst[0] = r0;
+        dst[1] = r1;
+    }
     int levels = 1;
     if (LAYOUT == BS_PPVBS) {
-        // mask words and BS_j prefixes for the groups whose selected rows reach byte j
+        const uint64_t w = t * kTileWords + lane;
         uint32_t reach = sel;  // selected rows that have byte j-1
-        for (int j = 2; j <= a.K; j++) {
+        for (int j = 2; j <= min(a.K, KMAX); j++) {
             const uint32_t bal = __ballot_sync(kFull, reach != 0u);
             if (!bal) break;
             const uint32_t gact = (bal >> (lane & 24u)) & 0xFFu;
@@ -208,7 +322,7 @@ __device__ __forceinline__ void gather_tile(const LookK &a, uint64_t t, uint64_t
             uint32_t inc = c;
 #pragma unroll
             for (int d = 1; d < 8; d <<= 1) {
-                uint32_t v = __shfl_up_sync(kFull, inc, d);
+                const uint32_t v = __shfl_up_sync(kFull, inc, d);
                 if ((lane & 7u) >= (uint32_t)d) inc += v;
             }
             const uint32_t goff = gact ? __ldg(a.off[j] + t * kGroupsPerTile + (lane >> 3)) : 0u;
@@ -219,79 +333,328 @@ __device__ __forceinline__ void gather_tile(const LookK &a, uint64_t t, uint64_t
         }
     }
     __syncwarp();
-    for (uint32_t i = lane; i < total; i += 32) {
-        const uint32_t q = sm.list[i];
-        const uint64_t row = t * kTileRows + q;
-        uint64_t code;
-        int len;
-        if (LAYOUT == BS_PPVBS) {
-            code = __ldg(a.dense + t * kTileRows + tile_pos(q));
-            len = 1;
-            const uint32_t wq = q >> 5, bq = q & 31u;
-            for (int j = 2; j <= levels; j++) {
-                const uint32_t m = sm.mask[j][wq];
-                if (!((m >> bq) & 1u)) break;
-                const uint64_t idx = (uint64_t)sm.pref[j][wq] + __popc(m & ((1u << bq) - 1u));
-                uint32_t byte = 0;
-                if (idx < a.deep_len[j]) byte = __ldg(a.deep[j] + idx);
-                else atomicOr(a.status, kStatusBounds);
-                code = (code << 8) | byte;
-                len = j;
-            }
-        } else if (LAYOUT == BS_BYTESLICE) {
-            uint64_t aligned = 0;
-            const uint64_t pos = t * kTileRows + tile_pos(q);
-            for (int s = 0; s < a.K; s++) aligned = (aligned << 8) | __ldg(a.dense + (uint64_t)s * a.slice_bytes + pos);
-            code = aligned >> (8 * a.K - a.k);
-            len = a.K;
-        } else {
-            const uint64_t bit = row * (uint64_t)a.k;
-            const uint32_t *p = a.packed + (bit >> 5);
-            const uint32_t lo = __ldg(p), hi = __ldg(p + 1);
-            code = __funnelshift_r(lo, hi, (uint32_t)(bit & 31u)) & (a.k == 32 ? kFull : ((1u << a.k) - 1u));
-            len = (a.k + 7) / 8;
+    if (kDenseOk && dense) {
+        gather_dense_vbs<KMAX>(a, t, sel, incl - cnt, total, levels, out_base, sm, val1, lane);
+        return;
+    }
+    for (uint32_t i0 = 0; i0 < total; i0 += 32 * kUnroll) {
+        uint64_t code[kUnroll];
+        int len[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+            code[u] = 0;
+            len[u] = 1;
+            if (i < total) fetch_code<LAYOUT, KMAX>(a, t, sm.list[i], levels, &sm, staged, code[u], len[u]);
         }
-        const uint64_t o = out_base + i;
-        if (o < a.out_cap) {
-            if (CODES) {
-                a.out_codes[o] = (LAYOUT == BS_PPVBS) ? (code << (8 * (a.K - len))) : code;
-            } else {
-                a.out_vals[o] = decode_value(a, code, len);
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+            const uint64_t o = out_base + i;
+            if (i < total && o < a.out_cap) {
+                if (CODES) a.out_codes[o] = LAYOUT == BS_PPVBS ? (code[u] << (8 * (a.K - len[u]))) : code[u];
+                else a.out_vals[o] = decode_value<LAYOUT>(a, code[u], len[u]);
             }
         }
     }
     __syncwarp();
 }
 
-template <int LAYOUT, bool CODES>
-__global__ void __launch_bounds__(kLookupThreads) lookup_gather_kernel(const LookK a) {
-    __shared__ WarpSmem smem[kLookupWarps];
-    __shared__ uint32_t tile_cnt[kChunkTiles];
+// ------------------------------------------------------------ 1. count
+__global__ void __launch_bounds__(kLookupThreads) lookup_count_kernel(const LookK a) {
+    __shared__ uint32_t part[kLookupWarps];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t chunk = blockIdx.x;
-    for (int i = 0; i < kTilesPerWarp; i++) {
-        const uint64_t t = (uint64_t)chunk * kChunkTiles + warp * kTilesPerWarp + i;
-        uint32_t c = 0;
-        if (t < a.n_tiles) {
-            const uint64_t w = t * kTileWords + lane;
-            const uint32_t vm = valid_mask(w * 32u, a.n);
-            if (vm) c = __popc(__ldg(a.bits + w) & vm);
+    const uint64_t chunk = (uint64_t)blockIdx.x * kGroupChunks + warp;
+    const uint64_t nwords = (a.n + 31) / 32;
+    uint32_t acc = 0;
+    if (chunk < a.n_chunks) {
+        // 512 words per chunk: lane reads 16 of them, as four 16-byte loads when
+        // the words are complete (no bit at or past n) and the vector is aligned
+        const uint64_t w0 = chunk * (uint64_t)kChunkTiles * kTileWords;
+        const uint64_t full = a.n / 32;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const uint64_t w = w0 + (uint64_t)(i * 32 + lane) * 4;
+            if (a.bits_vec && w + 4 <= full) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.bits + w));
+                acc += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            } else {
+                for (uint64_t x = w; x < w + 4 && x < nwords; x++)
+                    acc += __popc(__ldg(a.bits + x) & valid_mask(x * 32u, a.n));
+            }
         }
-        c = warp_sum(c);
-        if (lane == 0) tile_cnt[warp * kTilesPerWarp + i] = c;
+        acc = warp_sum(acc);
+        if (lane == 0) a.chunk_cnt[chunk] = acc;
     }
+    if (lane == 0) part[warp] = acc;
     __syncthreads();
-    uint64_t base = a.chunk[chunk];
-    for (uint32_t i = 0; i < warp * kTilesPerWarp; i++) base += tile_cnt[i];
-    for (int i = 0; i < kTilesPerWarp; i++) {
-        const uint64_t t = (uint64_t)chunk * kChunkTiles + warp * kTilesPerWarp + i;
-        if (t >= a.n_tiles) break;
-        if (base < a.out_cap) gather_tile<LAYOUT, CODES>(a, t, base, smem[warp], lane);
-        base += tile_cnt[warp * kTilesPerWarp + i];
+    if (threadIdx.x == 0) {
+        uint64_t s = 0;
+        for (int i = 0; i < kLookupWarps; i++) s += part[i];
+        a.group_off[blockIdx.x] = s;
+    }
+}
+
+// ------------------------------------------------------------ 2. scan
+__global__ void __launch_bounds__(kScanBlock) lookup_scan_kernel(const LookK a) {
+    __shared__ uint64_t warp_tot[kScanBlock / 32];
+    __shared__ uint64_t carry;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < a.n_groups; base += kScanBlock) {
+        const uint32_t i = base + tid;
+        const uint64_t v = i < a.n_groups ? a.group_off[i] : 0;
+        uint64_t incl = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t o = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (uint32_t)d) incl += o;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint64_t w = warp_tot[lane];
+            uint64_t wi = w;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint64_t o = __shfl_up_sync(kFull, wi, d);
+                if (lane >= (uint32_t)d) wi += o;
+            }
+            warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        const uint64_t excl = carry + warp_tot[warp] + incl - v;
+        if (i < a.n_groups) a.group_off[i] = excl;
+        __syncthreads();
+        if (tid == kScanBlock - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (tid == 0 && a.count) *a.count = carry;
+}
+
+// ------------------------------------------------------------ 3. gather
+// Code of one row with no shared-memory help: PP-VBS finds byte j at
+// off_j[group] + popcounts of the group's earlier mask words + rank in its word
+// (all within one 32-byte sector of M_j).
+template <int LAYOUT, int KMAX>
+__device__ __forceinline__ void row_code(const LookK &a, uint64_t row, uint64_t &code, int &len) {
+    const uint64_t t = row >> 10;
+    const uint32_t q = (uint32_t)(row & 1023u);
+    if (LAYOUT == BS_PPVBS) {
+        code = __ldg(a.dense + t * kTileRows + tile_pos(q));
+        len = 1;
+        const uint64_t g = row >> 8, w = row >> 5;
+        const uint32_t b = (uint32_t)(row & 31u), below = (1u << b) - 1u;
+        for (int j = 2; j <= min(a.K, KMAX); j++) {
+            const uint32_t mw = __ldg(a.mask[j] + w);
+            if (!((mw >> b) & 1u)) break;
+            uint64_t idx = __ldg(a.off[j] + g) + __popc(mw & below);
+            for (uint64_t x = g * kGroupWords; x < w; x++) idx += __popc(__ldg(a.mask[j] + x));
+            uint32_t byte = 0;
+            if (idx < a.deep_len[j]) byte = __ldg(a.deep[j] + idx);
+            else atomicOr(a.status, kStatusBounds);
+            code = (code << 8) | byte;
+            len = j;
+        }
+    } else {
+        fetch_code<LAYOUT, KMAX>(a, t, q, 1, (const WarpSmemT<KMAX> *)nullptr, false, code, len);
+    }
+}
+
+// Dense PP-VBS tile whose codes have at most two bytes: every load that does
+// not depend on another (the lane's 32 BS_1 bytes, its M_2 word, its group's
+// BS_2 offset and the tile's BS_2 segment bounds) is issued in one round; the
+// segment words and then the two-byte decode table follow. Each lane walks its
+// own selected rows in order and leaves a 16-bit key (first two code bytes) per
+// output slot; the warp then decodes the keys and stores them coalesced.
+__device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint32_t sel, uint64_t out_base,
+                                                WarpSmemT<2> &sm, const int32_t *val1, uint32_t lane) {
+    // round 1: independent loads
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.dense + t * kTileRows);
+    const uint4 v0 = __ldg(src + lane), v1 = __ldg(src + 32 + lane);
+    const bool has2 = a.K >= 2;
+    const uint32_t m2 = has2 ? __ldg(a.mask[2] + t * kTileWords + lane) : 0u;
+    const uint32_t goff = has2 ? __ldg(a.off[2] + t * kGroupsPerTile + (lane >> 3)) : 0u;
+    const uint32_t seg_lo = has2 ? __ldg(a.off[2] + t * kGroupsPerTile) : 0u;
+    const uint32_t seg_hi = has2 ? __ldg(a.off[2] + t * kGroupsPerTile + kGroupsPerTile) : 0u;
+    // ALU while they fly: output positions of this lane's rows
+    const uint32_t cnt = __popc(sel);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, d);
+        if (lane >= (uint32_t)d) incl += v;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t c2 = __popc(m2);
+    uint32_t inc2 = c2;
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, inc2, d);
+        if ((lane & 7u) >= (uint32_t)d) inc2 += v;
+    }
+    // round 2: the tile's BS_2 bytes (contiguous)
+    if (has2) {
+        const uint32_t w0 = seg_lo >> 2, w1 = (seg_hi + 3) >> 2;
+        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(a.deep[2]);
+        constexpr uint32_t kSegWords = sizeof(sm.seg) / 4;
+        for (uint32_t i = lane; i < w1 - w0 && i < kSegWords; i += 32) sm.seg[i] = __ldg(s32 + w0 + i);
+    }
+    uint4 r0, r1;
+    transpose_lane_bytes(v0, v1, r0, r1);
+    uint4 *dst = reinterpret_cast<uint4 *>(sm.dense + lane * 32u);
+    dst[0] = r0;
+    dst[1] = r1;
+    __syncwarp();
+    const uint8_t *seg = reinterpret_cast<const uint8_t *>(sm.seg) + (seg_lo & 3u);
+    const uint32_t p2 = goff + inc2 - c2 - seg_lo;  // lane's first BS_2 byte, relative to the segment
+    uint32_t pos = incl - cnt, r = sel;
+    while (r) {
+        const uint32_t b = __ffs(r) - 1;
+        r &= r - 1;
+        uint32_t key = (uint32_t)sm.dense[lane * 32u + b] << 8;
+        if ((m2 >> b) & 1u) key |= seg[p2 + __popc(m2 & ((1u << b) - 1u))];
+        sm.list[pos++] = (uint16_t)key;
+    }
+    __syncwarp();
+    // round 3: decode and store
+    for (uint32_t i0 = 0; i0 < total; i0 += 32 * kUnroll) {
+        int32_t v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+            v[u] = 0;
+            if (i < total) {
+                const uint32_t key = sm.list[i];
+                v[u] = (key & 0xFFu) ? __ldg(a.val2 + key) : val1[key >> 8];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+            const uint64_t o = out_base + i;
+            if (i < total && o < a.out_cap) a.out_vals[o] = v[u];
+        }
+    }
+    __syncwarp();
+}
+
+// A warp owns one chunk of 16 tiles; a CTA's 8 warps own one group of 8 chunks,
+// whose offset comes from the scan kernel. The warp reads the chunk's 512 bit
+// vector words at once. A sparse chunk (at most kSparseMax selected rows) lists
+// its rows in shared memory and resolves them all in parallel across lanes; a
+// dense chunk goes tile by tile.
+template <int LAYOUT, bool CODES, int KMAX>
+__global__ void __launch_bounds__(kLookupThreads, 5) lookup_gather_kernel(const LookK a) {
+    __shared__ WarpSmemT<KMAX> smem[kLookupWarps];
+    __shared__ int32_t val1[256];  // PP-VBS: value of every one-byte code
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    if (LAYOUT == BS_PPVBS && !CODES && threadIdx.x < 256) val1[threadIdx.x] = __ldg(a.val2 + (threadIdx.x << 8));
+    __syncthreads();
+    WarpSmemT<KMAX> &sm = smem[warp];
+    const uint64_t nwords = (a.n + 31) / 32;
+    for (uint32_t g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
+        const uint32_t c = g * kGroupChunks + warp;
+        if (c >= a.n_chunks) continue;
+        // chunk offset: group offset + counts of the earlier chunks of the group
+        const uint32_t cc = lane < warp ? __ldg(a.chunk_cnt + g * kGroupChunks + lane) : 0u;
+        uint64_t base = a.group_off[g] + warp_sum(cc);
+        // the chunk's words: block i (4 tiles) holds words i*128 + 4L + 0..3 at lane L
+        const uint64_t w0 = (uint64_t)c * kChunkTiles * kTileWords;
+        uint32_t wv[4][4];
+        uint32_t cnt[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            cnt[i] = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint64_t w = w0 + (uint64_t)(i * 128 + 4 * lane + k);
+                const uint32_t vm = w < nwords ? valid_mask(w * 32u, a.n) : 0u;
+                wv[i][k] = vm ? (__ldg(a.bits + w) & vm) : 0u;
+                cnt[i] += __popc(wv[i][k]);
+            }
+        }
+        const uint32_t chunk_total = warp_sum(cnt[0] + cnt[1] + cnt[2] + cnt[3]);
+        if (chunk_total == 0) continue;
+        if (chunk_total <= kSparseMax) {
+            // list the selected rows (row offset inside the chunk) in row order
+            uint32_t pos0 = 0;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                uint32_t incl = cnt[i];
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t v = __shfl_up_sync(kFull, incl, d);
+                    if (lane >= (uint32_t)d) incl += v;
+                }
+                uint32_t pos = pos0 + incl - cnt[i];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    uint32_t r = wv[i][k];
+                    while (r) {
+                        const uint32_t b = __ffs(r) - 1;
+                        r &= r - 1;
+                        sm.list[pos++] = (uint16_t)((i * 128 + 4 * lane + k) * 32 + b);
+                    }
+                }
+                pos0 += __shfl_sync(kFull, incl, 31);
+            }
+            __syncwarp();
+            const uint64_t row0 = (uint64_t)c * kChunkTiles * kTileRows;
+            for (uint32_t i0 = 0; i0 < chunk_total; i0 += 32 * kUnroll) {
+                uint64_t code[kUnroll];
+                int len[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; u++) {
+                    const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+                    code[u] = 0;
+                    len[u] = 1;
+                    if (i < chunk_total) row_code<LAYOUT, KMAX>(a, row0 + sm.list[i], code[u], len[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kUnroll; u++) {
+                    const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+                    const uint64_t o = base + i;
+                    if (i < chunk_total && o < a.out_cap) {
+                        if (CODES) a.out_codes[o] = LAYOUT == BS_PPVBS ? (code[u] << (8 * (a.K - len[u]))) : code[u];
+                        else if (LAYOUT == BS_PPVBS && len[u] == 1) a.out_vals[o] = val1[code[u] & 0xFFu];
+                        else a.out_vals[o] = decode_value<LAYOUT>(a, code[u], len[u]);
+                    }
+                }
+            }
+            __syncwarp();
+            continue;
+        }
+        // dense chunk: tile by tile (tile 4i + j is lanes 8j..8j+7 of block i)
+        uint32_t tcnt[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            uint32_t v = cnt[i];
+            v += __shfl_xor_sync(kFull, v, 1);
+            v += __shfl_xor_sync(kFull, v, 2);
+            v += __shfl_xor_sync(kFull, v, 4);
+            tcnt[i] = v;  // count of tile 4i + (lane >> 3)
+        }
+        for (int tt = 0; tt < kChunkTiles; tt++) {
+            const uint32_t tc = __shfl_sync(kFull, tcnt[tt >> 2], (tt & 3) * 8);
+            const uint64_t t = (uint64_t)c * kChunkTiles + tt;
+            if (tc && t < a.n_tiles && base < a.out_cap) {
+                const uint64_t w = t * kTileWords + lane;
+                const uint32_t vm = valid_mask(w * 32u, a.n);
+                const uint32_t sel = vm ? (__ldg(a.bits + w) & vm) : 0u;
+                if (LAYOUT == BS_PPVBS && !CODES && KMAX == 2 && tc >= kStageMin)
+                    gather_dense_k2(a, t, sel, base, reinterpret_cast<WarpSmemT<2> &>(sm), val1, lane);
+                else
+                    gather_tile<LAYOUT, CODES, KMAX>(a, t, sel, base, sm, val1, lane);
+            }
+            base += tc;
+        }
     }
 }
 
 // ------------------------------------------------------- lookup by row ids
+template <int LAYOUT>
 __global__ void lookup_rowids_kernel(const LookK a, const uint32_t *rowids, uint64_t m) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t row = rowids[i];
@@ -304,11 +667,10 @@ __global__ void lookup_rowids_kernel(const LookK a, const uint32_t *rowids, uint
         const uint32_t q = row & 1023u;
         uint64_t code;
         int len;
-        if (a.layout == BS_PPVBS) {
+        if (LAYOUT == BS_PPVBS) {
             code = __ldg(a.dense + t * kTileRows + tile_pos(q));
             len = 1;
-            const uint64_t g = row >> 8;
-            const uint64_t w = row >> 5;
+            const uint64_t g = row >> 8, w = row >> 5;
             const uint32_t b = row & 31u;
             for (int j = 2; j <= a.K; j++) {
                 const uint32_t mw = __ldg(a.mask[j] + w);
@@ -322,20 +684,10 @@ __global__ void lookup_rowids_kernel(const LookK a, const uint32_t *rowids, uint
                 code = (code << 8) | byte;
                 len = j;
             }
-        } else if (a.layout == BS_BYTESLICE) {
-            uint64_t aligned = 0;
-            const uint64_t pos = t * kTileRows + tile_pos(q);
-            for (int s = 0; s < a.K; s++) aligned = (aligned << 8) | __ldg(a.dense + (uint64_t)s * a.slice_bytes + pos);
-            code = aligned >> (8 * a.K - a.k);
-            len = a.K;
         } else {
-            const uint64_t bit = (uint64_t)row * (uint64_t)a.k;
-            const uint32_t *p = a.packed + (bit >> 5);
-            code = __funnelshift_r(__ldg(p), __ldg(p + 1), (uint32_t)(bit & 31u)) &
-                   (a.k == 32 ? kFull : ((1u << a.k) - 1u));
-            len = (a.k + 7) / 8;
+            fetch_code<LAYOUT, 4>(a, t, q, 1, (const WarpSmemT<4> *)nullptr, false, code, len);
         }
-        a.out_vals[i] = decode_value(a, code, len);
+        a.out_vals[i] = decode_value<LAYOUT>(a, code, len);
     }
 }
 
@@ -346,11 +698,10 @@ LookK make_args(const Column &c) {
     a.k = c.k;
     a.identity = c.identity ? 1 : 0;
     a.domain_min = c.domain_min;
-    a.root_leaf = c.root_leaf ? 1 : 0;
-    a.n_trie_nodes = (uint32_t)(c.trie.size() / kTrieNodeWords);
     a.n = c.n;
     a.n_tiles = c.n_tiles;
     a.n_chunks = (c.n_tiles + kChunkTiles - 1) / kChunkTiles;
+    a.n_groups = (a.n_chunks + kGroupChunks - 1) / kGroupChunks;
     a.dense = c.d_dense;
     a.slice_bytes = c.dense_slice_bytes();
     for (int j = 2; j <= c.K && c.layout == BS_PPVBS; j++) {
@@ -360,18 +711,38 @@ LookK make_args(const Column &c) {
         a.deep_len[j] = c.deep_len[j];
     }
     a.packed = c.d_packed;
-    a.trie = c.d_trie;
+    a.val2 = c.d_val2;
+    a.leaf2 = c.d_leaf2;
     a.dict = c.d_dict;
     a.dict_size = c.dict.size();
     return a;
 }
 
-template <bool CODES>
+template <int LAYOUT, bool CODES, int KMAX>
+void launch_gather_k(const LookK &a, cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto fn = lookup_gather_kernel<LAYOUT, CODES, KMAX>;
+    const uint64_t resident = (uint64_t)sm_count(dev) * blocks_per_sm((const void *)fn, kLookupThreads, 0, dev);
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(a.n_groups, resident));
+    fn<<<grid, kLookupThreads, 0, s>>>(a);
+}
+
+template <int LAYOUT, bool CODES>
 void launch_gather(const LookK &a, cudaStream_t s) {
+    if (LAYOUT == BS_PPVBS && a.K > 4) launch_gather_k<LAYOUT, CODES, 8>(a, s);
+    else if (a.K > 2) launch_gather_k<LAYOUT, CODES, 4>(a, s);
+    else launch_gather_k<LAYOUT, CODES, 2>(a, s);
+}
+
+template <bool CODES>
+void launch_kernels(const LookK &a, cudaStream_t s) {
+    lookup_count_kernel<<<a.n_groups, kLookupThreads, 0, s>>>(a);
+    lookup_scan_kernel<<<1, kScanBlock, 0, s>>>(a);
     switch (a.layout) {
-    case BS_PPVBS: lookup_gather_kernel<BS_PPVBS, CODES><<<a.n_chunks, kLookupThreads, 0, s>>>(a); break;
-    case BS_BYTESLICE: lookup_gather_kernel<BS_BYTESLICE, CODES><<<a.n_chunks, kLookupThreads, 0, s>>>(a); break;
-    default: lookup_gather_kernel<BS_BITPACKED, CODES><<<a.n_chunks, kLookupThreads, 0, s>>>(a); break;
+    case BS_PPVBS: launch_gather<BS_PPVBS, CODES>(a, s); break;
+    case BS_BYTESLICE: launch_gather<BS_BYTESLICE, CODES>(a, s); break;
+    default: launch_gather<BS_BITPACKED, CODES>(a, s); break;
     }
 }
 
@@ -379,14 +750,17 @@ void launch_gather(const LookK &a, cudaStream_t s) {
 
 uint64_t lookup_workspace_bytes(const Column &c) {
     const uint64_t chunks = ((uint64_t)c.n_tiles + kChunkTiles - 1) / kChunkTiles;
-    return std::max<uint64_t>(256, (chunks * 4 + 255) & ~255ull);
+    const uint64_t groups = (chunks + kGroupChunks - 1) / kGroupChunks;
+    return ((chunks * 4 + 255) & ~255ull) + ((groups * 8 + 255) & ~255ull);
 }
 
 int launch_lookup(const Column &c, const uint32_t *d_bits, int32_t *d_vals, uint64_t *d_codes, uint64_t out_cap,
                   uint64_t *d_count, void *d_ws, cudaStream_t s) {
     LookK a = make_args(c);
     a.bits = d_bits;
-    a.chunk = (uint32_t *)d_ws;
+    a.bits_vec = ((uintptr_t)d_bits & 15u) == 0;
+    a.chunk_cnt = (uint32_t *)d_ws;
+    a.group_off = (uint64_t *)((uint8_t *)d_ws + ((a.n_chunks * 4ull + 255) & ~255ull));
     a.out_vals = d_vals;
     a.out_codes = d_codes;
     a.out_cap = out_cap;
@@ -397,10 +771,9 @@ int launch_lookup(const Column &c, const uint32_t *d_bits, int32_t *d_vals, uint
         if (d_count && cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s) != cudaSuccess) return BS_ERR_CUDA;
         return BS_OK;
     }
-    lookup_count_kernel<<<a.n_chunks, kLookupThreads, 0, s>>>(a);
-    lookup_offsets_kernel<<<1, kScanBlock, 0, s>>>(a);
-    if (d_codes) launch_gather<true>(a, s);
-    else launch_gather<false>(a, s);
+    // every workspace word is written by the count kernel before it is read
+    if (d_codes) launch_kernels<true>(a, s);
+    else launch_kernels<false>(a, s);
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
 
@@ -414,7 +787,11 @@ int launch_lookup_rowids(const Column &c, const uint32_t *d_rowids, uint64_t m, 
     cudaGetDevice(&dev);
     const uint64_t want = (m + 255) / 256;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sm_count(dev) * 16));
-    lookup_rowids_kernel<<<grid, 256, 0, s>>>(a, d_rowids, m);
+    switch (c.layout) {
+    case BS_PPVBS: lookup_rowids_kernel<BS_PPVBS><<<grid, 256, 0, s>>>(a, d_rowids, m); break;
+    case BS_BYTESLICE: lookup_rowids_kernel<BS_BYTESLICE><<<grid, 256, 0, s>>>(a, d_rowids, m); break;
+    default: lookup_rowids_kernel<BS_BITPACKED><<<grid, 256, 0, s>>>(a, d_rowids, m); break;
+    }
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
 

@@ -4,10 +4,11 @@
 // Some callers cannot allocate device memory at lookup time: code that runs
 // while a CUDA graph is being built or replayed by someone else, hosts that
 // hand out a fixed memory budget up front, or real-time paths that must not
-// touch an allocator. This entry point allocates nothing. Its scratch (one
-// 32-bit counter per 16,384 rows, i.e. the per-chunk counts and offsets of the
-// three-kernel compaction) lives in the file-scope array below, so every GPU
-// that loads the library holds these 1 MiB until the process exits.
+// touch an allocator. This entry point allocates nothing. Its scratch (the
+// lookup's 32-bit count per 16,384 rows and 64-bit offset per 131,072 rows,
+// 1.25 MiB for the largest column) lives in the file-scope array below, so
+// every GPU that loads the library holds these 2 MiB + 4 KiB until the
+// process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -16,7 +17,7 @@
 
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = 1u << 20;  // 262,144 chunks: any column below 2^32 rows
+constexpr size_t kNoAllocScratchBytes = (1u << 21) + 4096;  // 262,144 chunks: any column below 2^32 rows
 
 static __device__ __align__(256) unsigned char g_lookup_scratch[kNoAllocScratchBytes];
 
@@ -60,10 +61,9 @@ extern "C" int bs_lookup_noalloc(const bs_column *col, const uint32_t *d_bits, i
     int rc = BS_OK;
     void *ws = scratch_on_current_device(&rc);
     if (ws) {
-        cudaStream_t s = (cudaStream_t)stream;
-        // the array keeps the previous call's contents: start from zero
-        if (cudaMemsetAsync(ws, 0, need, s) != cudaSuccess) rc = BS_ERR_CUDA;
-        if (rc == BS_OK) rc = bs::launch_lookup(c, d_bits, d_out, nullptr, out_cap, d_count, ws, s);
+        // the array keeps the previous call's contents; the lookup's count
+        // kernel writes every scratch word before anything reads it
+        rc = bs::launch_lookup(c, d_bits, d_out, nullptr, out_cap, d_count, ws, (cudaStream_t)stream);
     }
     if (prev != c.device) cudaSetDevice(prev);
     return rc;

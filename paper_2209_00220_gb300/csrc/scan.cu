@@ -37,6 +37,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "kernels.h"
 
@@ -92,6 +93,9 @@ __device__ __forceinline__ void st_stream(uint32_t *p, uint32_t v) {
 
 __device__ __forceinline__ void cp_async16(uint32_t smem_addr, const uint8_t *g) {
     asm volatile("cp.async.cg.shared.global.L2::256B [%0], [%1], 16;" ::"r"(smem_addr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t smem_addr, const uint32_t *g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr), "l"(g) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -178,9 +182,9 @@ __device__ __forceinline__ uint32_t final_bits(int op, uint32_t sd, uint32_t LT1
 }
 
 // ------------------------------------------------------- PP-VBS levels >= 2
-template <int NLIT>
-__device__ __noinline__ void vbs_deeper(const ScanK &a, uint32_t t, uint32_t lane, uint32_t &LT1, uint32_t &EQ1,
-                                        uint32_t &LT2, uint32_t &EQ2) {
+template <int NLIT, bool PF>
+__device__ __forceinline__ void vbs_deeper(const ScanK &a, uint32_t t, uint32_t lane, uint32_t m2_pre, uint32_t &LT1,
+                                           uint32_t &EQ1, uint32_t &LT2, uint32_t &EQ2) {
     const int K = a.K;
     const int l1 = (int)a.lit[0].len, e1 = a.lit[0].jend;
     const int l2 = NLIT == 2 ? (int)a.lit[1].len : 0, e2 = NLIT == 2 ? a.lit[1].jend : 1;
@@ -190,10 +194,16 @@ __device__ __noinline__ void vbs_deeper(const ScanK &a, uint32_t t, uint32_t lan
         const bool act1 = j <= e1, act2 = NLIT == 2 && j <= e2;
         const uint32_t pend = (act1 ? EQ1 : 0u) | (act2 ? EQ2 : 0u);
         if (!__any_sync(kFull, pend != 0u)) break;
-        // M_j only for 256-row groups (8 lanes) holding a pending row
-        const uint32_t bal = __ballot_sync(kFull, pend != 0u);
-        const uint32_t gact = (bal >> (lane & 24u)) & 0xFFu;
-        const uint32_t mj = gact ? __ldg(a.mask[j] + wbase + lane) : 0u;
+        // M_j only for 256-row groups (8 lanes) holding a pending row; M_2 may
+        // already be in shared memory (prefetched with the tile)
+        uint32_t mj;
+        if (PF && j == 2) {
+            mj = m2_pre;
+        } else {
+            const uint32_t bal = __ballot_sync(kFull, pend != 0u);
+            const uint32_t gact = (bal >> (lane & 24u)) & 0xFFu;
+            mj = gact ? __ldg(a.mask[j] + wbase + lane) : 0u;
+        }
         if (act1) {
             if (j <= l1) { LT1 |= EQ1 & ~mj; EQ1 &= mj; }   // row ends first: smaller
             else EQ1 &= ~mj;                               // row continues: larger; else equal
@@ -245,7 +255,7 @@ __device__ __noinline__ void vbs_deeper(const ScanK &a, uint32_t t, uint32_t lan
 
 // ---------------------------------------------------- ByteSlice slices >= 2
 template <int NLIT>
-__device__ __noinline__ void bsl_deeper(const ScanK &a, uint32_t t, uint32_t lane, uint32_t &LT1, uint32_t &EQ1,
+__device__ __forceinline__ void bsl_deeper(const ScanK &a, uint32_t t, uint32_t lane, uint32_t &LT1, uint32_t &EQ1,
                                         uint32_t &LT2, uint32_t &EQ2) {
     for (int j = 2; j <= a.K; j++) {
         const uint32_t pend = EQ1 | EQ2;
@@ -267,9 +277,9 @@ __device__ __noinline__ void bsl_deeper(const ScanK &a, uint32_t t, uint32_t lan
 }
 
 // One tile whose lane bytes are in x: byte 1, deeper levels, result word.
-template <bool VBS, int NLIT, bool HI0, bool HI1, bool NEED_EQ>
+template <bool VBS, int NLIT, bool HI0, bool HI1, bool NEED_EQ, bool PF>
 __device__ __forceinline__ void scan_tile(const ScanK &a, uint32_t t, uint32_t lane, const uint32_t x[8],
-                                          uint32_t sd, uint32_t add0, uint32_t add1) {
+                                          uint32_t sd, uint32_t add0, uint32_t add1, uint32_t m2_pre) {
     uint32_t GE1, EQ1 = 0, LT2 = 0, EQ2 = 0;
     cmp32_fast<HI0, HI1, NEED_EQ>(x, add0, add1, GE1, EQ1);
     uint32_t LT1 = sd & ~GE1;
@@ -281,7 +291,7 @@ __device__ __forceinline__ void scan_tile(const ScanK &a, uint32_t t, uint32_t l
     }
     if (NEED_EQ || NLIT == 2) {
         if (__any_sync(kFull, (EQ1 | EQ2) != 0u)) {
-            if (VBS) vbs_deeper<NLIT>(a, t, lane, LT1, EQ1, LT2, EQ2);
+            if (VBS) vbs_deeper<NLIT, PF>(a, t, lane, m2_pre, LT1, EQ1, LT2, EQ2);
             else bsl_deeper<NLIT>(a, t, lane, LT1, EQ1, LT2, EQ2);
         }
     }
@@ -289,9 +299,13 @@ __device__ __forceinline__ void scan_tile(const ScanK &a, uint32_t t, uint32_t l
     if (w * 32u < a.n) st_stream(a.out + w, final_bits(a.op, sd, LT1, EQ1, LT2, EQ2));
 }
 
-template <bool VBS, int NLIT, bool HI0, bool HI1, bool NEED_EQ>
+// PF: the tile's M_2 words travel in the ring with its BS_1 bytes (chosen on
+// the host when most tiles are expected to hold rows pending after byte 1).
+template <bool VBS, int NLIT, bool HI0, bool HI1, bool NEED_EQ, bool PF>
 __global__ void __launch_bounds__(kScanThreads) scan_dense_kernel(const ScanK a) {
-    __shared__ __align__(16) uint8_t ring[kScanWarps][kStages][kTileRows];
+    constexpr int kSlot = kTileRows + (PF ? kTileWords * 4 : 0);
+    static_assert(kSlot % 16 == 0, "ring slots receive 16-byte cp.async copies");
+    __shared__ __align__(16) uint8_t ring[kScanWarps][kStages][kSlot];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -306,7 +320,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_dense_kernel(const ScanK a)
             if (sd) sd &= __ldg(a.seed + w);
             uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (sd) load_lane32(a.dense + (uint64_t)t * kTileRows, lane, x);
-            scan_tile<VBS, NLIT, HI0, HI1, NEED_EQ>(a, t, lane, x, sd, add0, add1);
+            scan_tile<VBS, NLIT, HI0, HI1, NEED_EQ, false>(a, t, lane, x, sd, add0, add1, 0u);
         }
         return;
     }
@@ -316,9 +330,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_dense_kernel(const ScanK a)
     auto issue = [&](uint32_t t, int stage) {
         if (t < a.n_tiles) {
             const uint8_t *g = a.dense + (uint64_t)t * kTileRows;
-            const uint32_t s = sbase + (uint32_t)stage * kTileRows;
+            const uint32_t s = sbase + (uint32_t)stage * kSlot;
             cp_async16(s + lane * 16u, g + lane * 16u);
             cp_async16(s + 512u + lane * 16u, g + 512u + lane * 16u);
+            if (PF) cp_async4(s + kTileRows + lane * 4u, a.mask[2] + (uint64_t)t * kTileWords + lane);
         }
         cp_async_commit();  // empty groups keep the group count uniform
     };
@@ -328,54 +343,90 @@ __global__ void __launch_bounds__(kScanThreads) scan_dense_kernel(const ScanK a)
     for (uint32_t t = gw; t < a.n_tiles; t += nw) {
         issue(t + 2 * nw, (stage + 2) % kStages);
         cp_async_wait<kStages - 1>();
-        const uint4 *sp = reinterpret_cast<const uint4 *>(my + stage * kTileRows);
+        const uint8_t *slot = my + stage * kSlot;
+        const uint4 *sp = reinterpret_cast<const uint4 *>(slot);
         const uint4 v0 = sp[lane], v1 = sp[32 + lane];
         const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        const uint32_t m2 = PF ? reinterpret_cast<const uint32_t *>(slot + kTileRows)[lane] : 0u;
         const uint32_t sd = valid_mask(((uint64_t)t * kTileWords + lane) * 32u, a.n);
-        scan_tile<VBS, NLIT, HI0, HI1, NEED_EQ>(a, t, lane, x, sd, add0, add1);
+        scan_tile<VBS, NLIT, HI0, HI1, NEED_EQ, PF>(a, t, lane, x, sd, add0, add1, m2);
         stage = (stage + 1) % kStages;
     }
     cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------ Bit-Packed
-// Round m of a tile evaluates rows 32m..32m+31: their codes fill exactly k
-// stream words starting at word t*32k + m*k, which lanes 0..k-1 load together;
-// each lane then funnel-shifts its code out of two neighbouring words received
-// by shuffle, and one ballot gives result word m.
+// Lane L owns codes 32L..32L+31 of a tile; as 32 codes of k bits fill exactly k
+// words, its codes are the k stream words starting at tile word L*k, loaded
+// with 16-, 8- or 4-byte vector loads (k % 4 == 0, k even, k odd). With k a
+// template constant every code is extracted with constant shifts; the range
+// test (code - lo) <= span (unsigned) replaces the paper's cmpgt_epi32.
+// Tiles are processed two at a time for k <= 16 so twice the words are in
+// flight per warp.
+template <int KB>
+__device__ __forceinline__ void load_packed(const uint32_t *p, uint32_t w[KB]) {
+    if (KB % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < KB / 4; i++) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p) + i);
+            w[4 * i] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
+        }
+    } else if (KB % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < KB / 2; i++) {
+            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p) + i);
+            w[2 * i] = v.x; w[2 * i + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < KB; i++) w[i] = __ldg(p + i);
+    }
+}
+
+template <int KB>
+__device__ __forceinline__ uint32_t packed_bits(const uint32_t w[KB], uint32_t lo, uint32_t span) {
+    constexpr uint32_t kMask = KB == 32 ? 0xFFFFFFFFu : ((1u << KB) - 1u);
+    uint32_t res = 0;
+#pragma unroll
+    for (int i = 0; i < 32; i++) {
+        const int bit = i * KB, wi = bit >> 5, sh = bit & 31;
+        uint32_t code = w[wi] >> sh;
+        if (sh + KB > 32) code |= w[wi + 1] << (32 - sh);
+        code &= kMask;
+        res |= (uint32_t)((code - lo) <= span) << i;
+    }
+    return res;
+}
+
+template <int KB>
 __global__ void __launch_bounds__(kScanThreads) scan_packed_kernel(const ScanK a) {
+    constexpr int kPair = KB <= 16 ? 2 : 1;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t k = (uint32_t)a.k;
-    const uint32_t kmask = k == 32 ? kFull : ((1u << k) - 1u);
-    const uint32_t lobit = lane * k;
-    const uint32_t src = lobit >> 5, sh = lobit & 31u;
-    for (uint32_t t = gw; t < a.n_tiles; t += nw) {
-        const uint64_t w = (uint64_t)t * kTileWords + lane;
-        uint32_t sdw = valid_mask(w * 32u, a.n);
-        if (a.seed && sdw) sdw &= __ldg(a.seed + w);
-        uint32_t res = 0;
-        const uint32_t *tw = a.packed + (uint64_t)t * kTileWords * k;
-#pragma unroll 4
-        for (uint32_t m = 0; m < 32u; m++) {
-            const uint32_t sm = __shfl_sync(kFull, sdw, m);
-            if (sm == 0u) continue;
-            const uint32_t *rw = tw + m * k;
-            uint32_t code;
-            if (k == 32u) {
-                code = __ldg(rw + lane);
-            } else {
-                const uint32_t word = lane < k ? __ldg(rw + lane) : 0u;
-                const uint32_t lo = __shfl_sync(kFull, word, src);
-                const uint32_t hi = __shfl_sync(kFull, word, (src + 1u) & 31u);
-                code = __funnelshift_r(lo, hi, sh) & kmask;
-            }
-            const bool in = (uint64_t)code >= a.lo && (uint64_t)code <= a.hi;
-            const uint32_t b = __ballot_sync(kFull, in != (a.invert != 0)) & sm;
-            if (lane == m) res = b;
+    const uint32_t lo = (uint32_t)a.lo, span = (uint32_t)(a.hi - a.lo);
+    const bool empty = a.lo > a.hi;
+    for (uint32_t t0 = gw * kPair; t0 < a.n_tiles; t0 += nw * kPair) {
+        uint32_t w[kPair][KB];
+        uint32_t sd[kPair];
+#pragma unroll
+        for (int u = 0; u < kPair; u++) {
+            const uint32_t t = t0 + (uint32_t)u;
+            const uint64_t wd = (uint64_t)t * kTileWords + lane;
+            sd[u] = t < a.n_tiles ? valid_mask(wd * 32u, a.n) : 0u;
+            if (a.seed && sd[u]) sd[u] &= __ldg(a.seed + wd);
+            if (sd[u]) load_packed<KB>(a.packed + ((uint64_t)t * kTileWords + lane) * KB, w[u]);
         }
-        if (w * 32u < a.n) st_stream(a.out + w, res);
+#pragma unroll
+        for (int u = 0; u < kPair; u++) {
+            const uint32_t t = t0 + (uint32_t)u;
+            const uint64_t wd = (uint64_t)t * kTileWords + lane;
+            uint32_t res = 0;
+            if (sd[u] && !empty) res = packed_bits<KB>(w[u], lo, span);
+            if (a.invert) res = ~res;
+            res &= sd[u];
+            if (t < a.n_tiles && wd * 32u < a.n) st_stream(a.out + wd, res);
+        }
     }
 }
 
@@ -404,20 +455,28 @@ int grid_for(KernelFn kernel, uint32_t n_tiles, int device) {
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, cap));
 }
 
-template <bool VBS, int NLIT>
+template <bool VBS, int NLIT, bool PF>
 KernelFn pick_dense(bool hi0, bool hi1, bool need_eq) {
     const int sel = (hi0 ? 4 : 0) | (hi1 ? 2 : 0) | (need_eq ? 1 : 0);
     switch (sel) {
-    case 0: return scan_dense_kernel<VBS, NLIT, false, false, false>;
-    case 1: return scan_dense_kernel<VBS, NLIT, false, false, true>;
-    case 2: return scan_dense_kernel<VBS, NLIT, false, true, false>;
-    case 3: return scan_dense_kernel<VBS, NLIT, false, true, true>;
-    case 4: return scan_dense_kernel<VBS, NLIT, true, false, false>;
-    case 5: return scan_dense_kernel<VBS, NLIT, true, false, true>;
-    case 6: return scan_dense_kernel<VBS, NLIT, true, true, false>;
-    default: return scan_dense_kernel<VBS, NLIT, true, true, true>;
+    case 0: return scan_dense_kernel<VBS, NLIT, false, false, false, PF>;
+    case 1: return scan_dense_kernel<VBS, NLIT, false, false, true, PF>;
+    case 2: return scan_dense_kernel<VBS, NLIT, false, true, false, PF>;
+    case 3: return scan_dense_kernel<VBS, NLIT, false, true, true, PF>;
+    case 4: return scan_dense_kernel<VBS, NLIT, true, false, false, PF>;
+    case 5: return scan_dense_kernel<VBS, NLIT, true, false, true, PF>;
+    case 6: return scan_dense_kernel<VBS, NLIT, true, true, false, PF>;
+    default: return scan_dense_kernel<VBS, NLIT, true, true, true, PF>;
     }
 }
+
+template <int... Ks>
+KernelFn packed_table(int k, std::integer_sequence<int, Ks...>) {
+    KernelFn fns[] = {scan_packed_kernel<Ks + 1>...};
+    return (k >= 1 && k <= 32) ? fns[k - 1] : nullptr;
+}
+
+KernelFn packed_kernel_for(int k) { return packed_table(k, std::make_integer_sequence<int, 32>{}); }
 
 DLit make_dlit(const LitCode &l) {
     DLit d{};
@@ -466,7 +525,9 @@ int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_
         case BS_NE: a.lo = c1; a.hi = c1; a.invert = 1; break;
         default: a.lo = c1; a.hi = c2; break;
         }
-        scan_packed_kernel<<<grid_for(scan_packed_kernel, c.n_tiles, dev), kScanThreads, 0, s>>>(a);
+        KernelFn fn = packed_kernel_for(c.k);
+        if (!fn) return BS_ERR_INVALID_ARG;
+        fn<<<grid_for(fn, (c.n_tiles + 1) / 2, dev), kScanThreads, 0, s>>>(a);
         return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
     }
     a.dense = c.d_dense;
@@ -499,11 +560,26 @@ int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_
     }
     const uint32_t cb = (uint32_t)(a.lit[0].left >> 56);
     const bool hi0 = cb >= 128u, hi1 = cb + 1 >= 128u;
+    // prefetch M_2 with every tile when rows sharing the literal's first byte are
+    // common enough that nearly every tile has some (more than ~4 per tile)
+    bool pf = false;
+    if (c.layout == BS_PPVBS && c.K >= 2 && (eq_at_1 || nlit == 2) && !d_seed) {
+        uint64_t share = 0;
+        const uint32_t b0 = cb, b1 = (uint32_t)(a.lit[1].left >> 56);
+        if (c.first_byte_rows.size() == 256) {
+            share = c.first_byte_rows[b0] + (nlit == 2 && b1 != b0 ? c.first_byte_rows[b1] : 0);
+            pf = share * (uint64_t)kTileRows > 4 * c.n;
+        } else {
+            pf = true;  // raw-code column: no statistics
+        }
+    }
     KernelFn fn;
-    if (c.layout == BS_PPVBS)
-        fn = nlit == 2 ? pick_dense<true, 2>(hi0, hi1, true) : pick_dense<true, 1>(hi0, hi1, eq_at_1);
-    else
-        fn = nlit == 2 ? pick_dense<false, 2>(hi0, hi1, true) : pick_dense<false, 1>(hi0, hi1, eq_at_1);
+    if (c.layout == BS_PPVBS) {
+        if (pf) fn = nlit == 2 ? pick_dense<true, 2, true>(hi0, hi1, true) : pick_dense<true, 1, true>(hi0, hi1, eq_at_1);
+        else fn = nlit == 2 ? pick_dense<true, 2, false>(hi0, hi1, true) : pick_dense<true, 1, false>(hi0, hi1, eq_at_1);
+    } else {
+        fn = nlit == 2 ? pick_dense<false, 2, false>(hi0, hi1, true) : pick_dense<false, 1, false>(hi0, hi1, eq_at_1);
+    }
     fn<<<grid_for(fn, c.n_tiles, dev), kScanThreads, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
