@@ -272,6 +272,60 @@ typedef struct {
 int bs_advise_layout(const int32_t *h_values, uint64_t n, int32_t mode, const bs_encode_opts *opts,
                      bs_advice *out);
 
+/* ------------------------------------------------------- batched form */
+
+#define BS_MAX_CONJ 4
+
+/* One request of a batch: a conjunction of 1..BS_MAX_CONJ predicates over
+ * columns of equal length (pipelined bit vectors, Section 3.3.1), then the
+ * lookup (Section 2.2, Algorithm 4) of the selected rows of `proj`. */
+typedef struct {
+    int32_t npreds;
+    int32_t reserved;
+    bs_pred preds[BS_MAX_CONJ];
+    const bs_column *proj;  /* column looked up (same length); NULL = preds[0].col */
+    int32_t *d_out;         /* device int32[out_cap]: values in ascending row order */
+    uint64_t out_cap;
+    uint64_t *d_count;      /* device uint64: number of selected rows (may exceed out_cap); may be NULL */
+    uint32_t *d_bits;       /* optional device bit vector (ceil(n/32) words) receiving the scan
+                               result; NULL = batch-owned scratch */
+} bs_request;
+
+/* Shape of the batched launch (NULL = defaults).
+ *   threads: 128, 256 or 512 threads per CTA; 0 = the tuned (or default 256) shape.
+ *   blocks_per_sm: CTAs per SM, 0 = as many as fit (all CTAs are co-resident).
+ *   autotune: 1 = time the candidate shapes on this batch and keep the fastest;
+ *             the choice is cached per batch signature in tune_cache.
+ *   use_graph: 1 (default) = capture the launch in a CUDA graph, 0 = launch directly.
+ *   tune_cache: JSON-lines cache file, NULL = $BS_TUNE_CACHE (or no cache). */
+typedef struct {
+    int32_t threads;
+    int32_t blocks_per_sm;
+    int32_t autotune;
+    int32_t use_graph;
+    const char *tune_cache;
+} bs_batch_opts;
+
+typedef struct bs_batch bs_batch; /* opaque: descriptors, scratch, captured graph */
+
+/* Prepare a batch of nreq requests (1..65536) for repeated launches: encodes
+ * every literal, uploads the request descriptors, allocates the batch scratch
+ * (bit vectors not supplied by the caller, per-chunk counts and offsets) and
+ * captures one persistent cooperative kernel in a CUDA graph. All columns must
+ * live on the same device. Output buffers stay owned by the caller and must
+ * outlive the batch. Errors: INVALID_ARG, UNSUPPORTED (raw-code column), OOM,
+ * CUDA. Not part of the paper: its batched launch has no counterpart there. */
+int bs_batch_create(const bs_request *reqs, int32_t nreq, const bs_batch_opts *opts, bs_batch **out);
+
+/* Run every request of the batch with one launch (one graph launch, or one
+ * cooperative kernel launch), stream-ordered. */
+int bs_batch_launch(bs_batch *b, void *stream);
+
+/* The shape the batch runs with: threads per CTA, CTAs, graph captured (0/1). */
+int bs_batch_info(const bs_batch *b, int32_t *threads, int32_t *ctas, int32_t *graph);
+
+void bs_batch_free(bs_batch *b);
+
 /* -------------------------------------------------------- diagnostics */
 
 const char *bs_strerror(int status);

@@ -54,6 +54,16 @@ class bs_lookup_bytes_t(ctypes.Structure):
                 ("dense_bytes", _u64), ("mask_bytes", _u64), ("offset_bytes", _u64), ("deep_bytes", _u64)]
 
 
+class bs_request(ctypes.Structure):
+    _fields_ = [("npreds", _i32), ("reserved", _i32), ("preds", bs_pred * 4), ("proj", _vp), ("d_out", _vp),
+                ("out_cap", _u64), ("d_count", _vp), ("d_bits", _vp)]
+
+
+class bs_batch_opts(ctypes.Structure):
+    _fields_ = [("threads", _i32), ("blocks_per_sm", _i32), ("autotune", _i32), ("use_graph", _i32),
+                ("tune_cache", ctypes.c_char_p)]
+
+
 class bs_advice(ctypes.Structure):
     _fields_ = [("layout", _i32), ("n_points", _i32), ("auc_byteslice", ctypes.c_double),
                 ("auc_ppvbs", ctypes.c_double), ("selectivity", ctypes.c_double * 100),
@@ -79,6 +89,10 @@ _SIGS = {
     "bs_advise_layout": ([_vp, _u64, _i32, _vp, _vp], _i32),
     "bs_scan_bytes": ([_vp, _i32, _i32, _i32, _vp, _vp], _i32),
     "bs_lookup_bytes": ([_vp, _vp, _vp], _i32),
+    "bs_batch_create": ([_vp, _i32, _vp, _vp], _i32),
+    "bs_batch_launch": ([_vp, _vp], _i32),
+    "bs_batch_info": ([_vp, _vp, _vp, _vp], _i32),
+    "bs_batch_free": ([_vp], None),
     "bs_strerror": ([_i32], ctypes.c_char_p),
     "bs_last_device_error": ([], _i32),
     "bs_version": ([], ctypes.c_char_p),
@@ -358,6 +372,76 @@ def bs_lookup_bytes(col: Column, bits) -> dict:
     _check(lib().bs_lookup_bytes(col.handle, b.ctypes.data if b.size else None, ctypes.byref(r)),
            "bs_lookup_bytes")
     return _struct_dict(r)
+
+
+# ----------------------------------------------------------------- batches
+class Batch:
+    """A prepared batch (bs_batch): many conjunction + lookup requests run by one
+    persistent launch. Keeps the request columns and output tensors alive."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        _check(lib().bs_batch_launch(self.handle, _stream(stream)), "bs_batch_launch")
+
+    def info(self) -> dict:
+        t, c, g = _i32(), _i32(), _i32()
+        _check(lib().bs_batch_info(self.handle, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g)), "bs_batch_info")
+        return {"threads": t.value, "ctas": c.value, "graph": bool(g.value)}
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.bs_batch_free(h)
+
+    def free(self):
+        self.__del__()
+
+
+def bs_batch_create(requests, threads: int = 0, blocks_per_sm: int = 0, autotune: bool = False,
+                    use_graph: bool = True, tune_cache: str | None = None) -> Batch:
+    """requests: sequence of dicts with keys
+         preds: [(Column, op, lit[, lit2]), ...]  (1..4, equal-length columns)
+         out:   torch int32 CUDA tensor (capacity = its numel unless out_cap given)
+         count: torch int64 CUDA tensor of 1 element (optional)
+         proj:  Column looked up (optional, default preds[0]'s column)
+         bits:  torch int32 CUDA tensor receiving the bit vector (optional)"""
+    arr = (bs_request * len(requests))()
+    keep = []
+    for i, q in enumerate(requests):
+        preds = q["preds"]
+        arr[i].npreds = len(preds)
+        for j, p in enumerate(preds):
+            arr[i].preds[j].col = p[0].handle
+            arr[i].preds[j].op = OPS[p[1]]
+            arr[i].preds[j].lit = int(p[2])
+            arr[i].preds[j].lit2 = int(p[3]) if len(p) > 3 else 0
+            keep.append(p[0])
+        proj = q.get("proj")
+        arr[i].proj = proj.handle if proj is not None else None
+        out = q.get("out")
+        arr[i].d_out = _dptr(out)
+        arr[i].out_cap = int(q.get("out_cap", out.numel() if out is not None else 0))
+        arr[i].d_count = _dptr(q.get("count"))
+        arr[i].d_bits = _dptr(q.get("bits"))
+        keep.extend([proj, out, q.get("count"), q.get("bits")])
+    o = bs_batch_opts()
+    o.threads, o.blocks_per_sm = int(threads), int(blocks_per_sm)
+    o.autotune, o.use_graph = 1 if autotune else 0, 1 if use_graph else 0
+    o.tune_cache = tune_cache.encode() if tune_cache else None
+    h = _vp()
+    _check(lib().bs_batch_create(arr, len(requests), ctypes.byref(o), ctypes.byref(h)), "bs_batch_create")
+    return Batch(h.value, keep)
+
+
+def bs_batch_launch(batch: Batch, stream=None):
+    batch.launch(stream)
+
+
+def bs_batch_free(batch: Batch):
+    batch.free()
 
 
 # ----------------------------------------------------------------- advisor

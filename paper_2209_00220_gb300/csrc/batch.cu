@@ -1,0 +1,586 @@
+// Batched form: many scan + lookup requests in one persistent, cooperative,
+// CUDA-graph-captured launch (the paper has no counterpart; it serves the
+// batched and serving workloads).
+//
+// One kernel, three phases separated by grid-wide barriers (cooperative
+// launch, so every CTA is resident; the barrier is an arrival counter polled
+// with acquire loads and an iteration cap that records a timeout instead of
+// waiting forever):
+//   1. scan   -- warps claim (request, chunk of 16 tiles) units from an atomic
+//               counter, so columns of uneven length share the GPU evenly. Per
+//               tile, the request's predicates run in order with the running
+//               result as the seed held in registers (the pipelined bit vectors
+//               of Section 3.3.1 without a round trip through memory; a tile
+//               whose rows are all decided stops early). The final bit vector
+//               word is stored and the chunk's selected rows are counted.
+//   2. offsets -- one CTA per request turns its chunk counts into exclusive
+//               offsets and writes the request's selected-row count.
+//   3. gather -- warps claim units again and run the lookup's chunk gather
+//               (lookup_dev.cuh) at the chunk's offset.
+// The host encodes every literal, uploads the request descriptors, sizes the
+// scratch, picks the launch shape (threads per CTA, CTAs per SM -- timed on the
+// batch itself when autotuning, with the winner cached per batch signature in a
+// JSON-lines file) and captures the counter reset plus the kernel in a graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lookup_dev.cuh"
+#include "scan_dev.cuh"
+
+namespace bs {
+namespace {
+
+constexpr int kMaxPreds = BS_MAX_CONJ;
+
+struct BPred {
+    ScanK a;
+    ScanPlan plan;
+};
+
+struct BReq {
+    BPred pred[kMaxPreds];
+    int32_t npred;
+    int32_t kmax;
+    LookK look;             // projection column view + bits, outputs
+    const int32_t *val1;    // projection is PP-VBS: one-byte code values
+    uint32_t *bits;         // result bit vector (ceil(n/32) words)
+    uint32_t *chunk_cnt;    // per chunk: selected rows, then (phase 2) unchanged
+    uint64_t *chunk_off;    // per chunk: first output slot
+    uint32_t n_chunks;
+    uint32_t unit0;         // first unit of this request
+};
+
+struct BatchK {
+    const BReq *reqs;
+    const uint32_t *unit0;  // nreq + 1 entries: prefix of chunk counts
+    int32_t nreq;
+    uint32_t total_units;
+    uint32_t *ctr;          // [0] scan units claimed, [1] gather units claimed, [2] barrier arrivals
+    uint32_t *status;
+};
+
+union WarpSmemAny {
+    WarpSmemT<2> k2;
+    WarpSmemT<4> k4;
+    WarpSmemT<8> k8;
+};
+
+// ---------------------------------------------------------- predicate tile
+template <int KB>
+__device__ __forceinline__ uint32_t packed_tile(const ScanK &a, uint32_t t, uint32_t lane, uint32_t sd) {
+    uint32_t w[KB];
+    load_packed<KB>(a.packed + ((uint64_t)t * kTileWords + lane) * KB, w);
+    uint32_t res = a.lo > a.hi ? 0u : packed_bits<KB>(w, (uint32_t)a.lo, (uint32_t)(a.hi - a.lo));
+    if (a.invert) res = ~res;
+    return res & sd;
+}
+
+__device__ __noinline__ uint32_t packed_dispatch(const ScanK &a, int k, uint32_t t, uint32_t lane, uint32_t sd) {
+    switch (k) {
+#define BS_PK(K) \
+    case K: return packed_tile<K>(a, t, lane, sd);
+        BS_PK(1) BS_PK(2) BS_PK(3) BS_PK(4) BS_PK(5) BS_PK(6) BS_PK(7) BS_PK(8)
+        BS_PK(9) BS_PK(10) BS_PK(11) BS_PK(12) BS_PK(13) BS_PK(14) BS_PK(15) BS_PK(16)
+        BS_PK(17) BS_PK(18) BS_PK(19) BS_PK(20) BS_PK(21) BS_PK(22) BS_PK(23) BS_PK(24)
+        BS_PK(25) BS_PK(26) BS_PK(27) BS_PK(28) BS_PK(29) BS_PK(30) BS_PK(31) BS_PK(32)
+#undef BS_PK
+    default: return 0u;
+    }
+}
+
+template <bool VBS, int NLIT>
+__device__ __noinline__ uint32_t dense_dispatch(const ScanK &a, const ScanPlan &pl, uint32_t t, uint32_t lane,
+                                                const uint32_t x[8], uint32_t sd) {
+    const uint32_t c0 = lit_byte(a.lit[0], 1);
+    const uint32_t add0 = thr_add(c0), add1 = thr_add(c0 + 1);
+    const int sel = (pl.hi0 ? 4 : 0) | (pl.hi1 ? 2 : 0) | (pl.eq1 ? 1 : 0);
+    switch (sel) {
+    case 0: return scan_tile<VBS, NLIT, false, false, false, false>(a, t, lane, x, sd, add0, add1, 0u);
+    case 1: return scan_tile<VBS, NLIT, false, false, true, false>(a, t, lane, x, sd, add0, add1, 0u);
+    case 2: return scan_tile<VBS, NLIT, false, true, false, false>(a, t, lane, x, sd, add0, add1, 0u);
+    case 3: return scan_tile<VBS, NLIT, false, true, true, false>(a, t, lane, x, sd, add0, add1, 0u);
+    case 4: return scan_tile<VBS, NLIT, true, false, false, false>(a, t, lane, x, sd, add0, add1, 0u);
+    case 5: return scan_tile<VBS, NLIT, true, false, true, false>(a, t, lane, x, sd, add0, add1, 0u);
+    case 6: return scan_tile<VBS, NLIT, true, true, false, false>(a, t, lane, x, sd, add0, add1, 0u);
+    default: return scan_tile<VBS, NLIT, true, true, true, false>(a, t, lane, x, sd, add0, add1, 0u);
+    }
+}
+
+// One predicate on one tile, restricted to the rows of sd (warp-wide call).
+__device__ __forceinline__ uint32_t pred_tile(const BPred &P, uint32_t t, uint32_t lane, uint32_t sd) {
+    const ScanPlan &pl = P.plan;
+    const ScanK &a = P.a;
+    if (pl.kind == ScanPlan::kFill) return a.fill_all ? sd : 0u;
+    if (pl.kind == ScanPlan::kPacked) return sd ? packed_dispatch(a, pl.k, t, lane, sd) : 0u;
+    uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (sd) load_lane32(a.dense + (uint64_t)t * kTileRows, lane, x);
+    if (pl.vbs) return pl.nlit == 2 ? dense_dispatch<true, 2>(a, pl, t, lane, x, sd)
+                                    : dense_dispatch<true, 1>(a, pl, t, lane, x, sd);
+    return pl.nlit == 2 ? dense_dispatch<false, 2>(a, pl, t, lane, x, sd)
+                        : dense_dispatch<false, 1>(a, pl, t, lane, x, sd);
+}
+
+__device__ __forceinline__ uint32_t find_request(const BatchK &b, uint32_t u) {
+    int lo = 0, hi = b.nreq - 1;  // largest r with unit0[r] <= u
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(b.unit0 + mid) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return (uint32_t)lo;
+}
+
+__device__ __forceinline__ uint32_t claim(uint32_t *ctr, uint32_t lane) {
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(ctr, 1u);
+    return __shfl_sync(kFull, u, 0);
+}
+
+template <int KMAX>
+__device__ __forceinline__ void gather_any(const LookK &a, uint32_t c, uint64_t base, WarpSmemT<KMAX> &sm,
+                                           const int32_t *val1, uint32_t lane) {
+    switch (a.layout) {
+    case BS_PPVBS: gather_chunk<BS_PPVBS, false, KMAX>(a, c, base, sm, val1, lane); break;
+    case BS_BYTESLICE: gather_chunk<BS_BYTESLICE, false, KMAX>(a, c, base, sm, val1, lane); break;
+    default: gather_chunk<BS_BITPACKED, false, KMAX>(a, c, base, sm, val1, lane); break;
+    }
+}
+
+__device__ __forceinline__ uint32_t ld_acquire32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier number `round` (1, 2, ...): every CTA adds one arrival and
+// waits until all gridDim.x * round arrivals are in.
+__device__ void grid_barrier(const BatchK &b, uint32_t round) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(b.ctr + 2, 1u);
+        const uint32_t target = gridDim.x * round;
+        uint32_t spins = 0;
+        while (ld_acquire32(b.ctr + 2) < target) {
+            if (++spins > (1u << 24)) {
+                atomicOr(b.status, kStatusTimeout);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__global__ void batch_kernel(const BatchK b) {
+    extern __shared__ __align__(16) unsigned char batch_smem[];
+    __shared__ uint64_t warp_tot[32];
+    __shared__ uint64_t carry;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    WarpSmemAny &sm = reinterpret_cast<WarpSmemAny *>(batch_smem)[warp];
+
+    // ---- phase 1: scan every request's chunks
+    for (;;) {
+        const uint32_t u = claim(b.ctr + 0, lane);
+        if (u >= b.total_units) break;
+        const uint32_t r = find_request(b, u);
+        const BReq &R = b.reqs[r];
+        const uint32_t c = u - R.unit0;
+        const uint64_t n = R.look.n;
+        uint32_t cnt = 0;
+        for (uint32_t tt = 0; tt < (uint32_t)kChunkTiles; tt++) {
+            const uint64_t t = (uint64_t)c * kChunkTiles + tt;
+            if (t >= R.look.n_tiles) break;
+            const uint64_t w = t * kTileWords + lane;
+            uint32_t sd = valid_mask(w * 32u, n);
+            for (int p = 0; p < R.npred; p++) {
+                if (!__any_sync(kFull, sd != 0u)) break;  // every row of the tile decided
+                sd = pred_tile(R.pred[p], (uint32_t)t, lane, sd);
+            }
+            if (w * 32u < n) R.bits[w] = sd;
+            cnt += __popc(sd);
+        }
+        cnt = warp_sum(cnt);
+        if (lane == 0) R.chunk_cnt[c] = cnt;
+    }
+    grid_barrier(b, 1);
+
+    // ---- phase 2: chunk offsets, one CTA per request
+    for (int r = blockIdx.x; r < b.nreq; r += gridDim.x) {
+        const BReq &R = b.reqs[r];
+        if (threadIdx.x == 0) carry = 0;
+        __syncthreads();
+        for (uint32_t s0 = 0; s0 < R.n_chunks; s0 += blockDim.x) {
+            const uint32_t i = s0 + threadIdx.x;
+            const uint64_t v = i < R.n_chunks ? R.chunk_cnt[i] : 0u;
+            uint64_t incl = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint64_t o = __shfl_up_sync(kFull, incl, d);
+                if (lane >= (uint32_t)d) incl += o;
+            }
+            if (lane == 31) warp_tot[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                const uint64_t wt = lane < nwarp ? warp_tot[lane] : 0u;
+                uint64_t wi = wt;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint64_t o = __shfl_up_sync(kFull, wi, d);
+                    if (lane >= (uint32_t)d) wi += o;
+                }
+                if (lane < nwarp) warp_tot[lane] = wi - wt;
+            }
+            __syncthreads();
+            const uint64_t excl = carry + warp_tot[warp] + incl - v;
+            if (i < R.n_chunks) R.chunk_off[i] = excl;
+            __syncthreads();
+            if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && R.look.count) *R.look.count = carry;
+        __syncthreads();
+    }
+    grid_barrier(b, 2);
+
+    // ---- phase 3: gather every request's chunks
+    for (;;) {
+        const uint32_t u = claim(b.ctr + 1, lane);
+        if (u >= b.total_units) break;
+        const uint32_t r = find_request(b, u);
+        const BReq &R = b.reqs[r];
+        const uint32_t c = u - R.unit0;
+        const uint64_t base = R.chunk_off[c];
+        if (base >= R.look.out_cap) continue;
+        if (R.kmax == 2) gather_any<2>(R.look, c, base, sm.k2, R.val1, lane);
+        else if (R.kmax == 4) gather_any<4>(R.look, c, base, sm.k4, R.val1, lane);
+        else gather_any<8>(R.look, c, base, sm.k8, R.val1, lane);
+    }
+}
+
+// ------------------------------------------------------------- tuning cache
+std::mutex g_tune_mu;
+
+std::string tune_path(const bs_batch_opts &o) {
+    if (o.tune_cache && *o.tune_cache) return o.tune_cache;
+    const char *e = std::getenv("BS_TUNE_CACHE");
+    return e ? std::string(e) : std::string();
+}
+
+bool tune_lookup(const std::string &path, const std::string &key, int &threads, int &bps) {
+    if (path.empty()) return false;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    FILE *f = std::fopen(path.c_str(), "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        char k[512];
+        int t = 0, b = 0;
+        // {"key": "...", "threads": T, "blocks_per_sm": B, ...}
+        if (std::sscanf(line, " {\"key\": \"%511[^\"]\", \"threads\": %d, \"blocks_per_sm\": %d", k, &t, &b) == 3 &&
+            key == k) {
+            threads = t;
+            bps = b;
+            found = true;  // the last entry for a key wins
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_store(const std::string &path, const std::string &key, int threads, int bps, double us) {
+    if (path.empty()) return;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    FILE *f = std::fopen(path.c_str(), "a");
+    if (!f) return;
+    std::fprintf(f, "{\"key\": \"%s\", \"threads\": %d, \"blocks_per_sm\": %d, \"us\": %.2f}\n", key.c_str(), threads,
+                 bps, us);
+    std::fclose(f);
+}
+
+size_t smem_bytes(int threads) { return (size_t)(threads / 32) * sizeof(WarpSmemAny); }
+
+}  // namespace
+}  // namespace bs
+
+// ================================================================ host API
+struct bs_batch {
+    int device = 0;
+    int nreq = 0;
+    void *d_arena = nullptr;
+    bs::BatchK k{};
+    int threads = 256;
+    int ctas = 0;
+    bool use_graph = true;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    bool graph_ok = false;
+};
+
+namespace {
+
+int launch_direct(bs_batch *b, cudaStream_t s) {
+    if (cudaMemsetAsync(b->k.ctr, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return BS_ERR_CUDA;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)b->ctas);
+    cfg.blockDim = dim3((unsigned)b->threads);
+    cfg.dynamicSmemBytes = bs::smem_bytes(b->threads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, bs::batch_kernel, b->k);
+    return e == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
+int shape(bs_batch *b, int threads, int bps) {
+    if (threads != 128 && threads != 256 && threads != 512) return BS_ERR_INVALID_ARG;
+    const size_t smem = bs::smem_bytes(threads);
+    if (cudaFuncSetAttribute(bs::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return BS_ERR_CUDA;
+    }
+    int fit = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, bs::batch_kernel, threads, smem) != cudaSuccess ||
+        fit < 1) {
+        cudaGetLastError();
+        return BS_ERR_CUDA;
+    }
+    const int per_sm = bps > 0 ? std::min(bps, fit) : fit;
+    b->threads = threads;
+    b->ctas = per_sm * bs::sm_count(b->device);
+    return BS_OK;
+}
+
+int capture(bs_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_ok = false;
+    if (!b->use_graph) return BS_OK;
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return BS_ERR_CUDA;
+    int rc = BS_OK;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = BS_ERR_CUDA;
+    if (rc == BS_OK) {
+        const int lrc = launch_direct(b, s);
+        const cudaError_t e = cudaStreamEndCapture(s, &b->graph);
+        if (lrc != BS_OK || e != cudaSuccess) rc = BS_ERR_CUDA;
+    }
+    if (rc == BS_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) rc = BS_ERR_CUDA;
+    cudaStreamDestroy(s);
+    if (rc != BS_OK) {
+        // graph capture of the cooperative launch is not available: launch directly
+        cudaGetLastError();
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+        b->exec = nullptr;
+        return BS_OK;
+    }
+    b->graph_ok = true;
+    return BS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bs_batch_create(const bs_request *reqs, int32_t nreq, const bs_batch_opts *opts, bs_batch **out) {
+    using namespace bs;
+    if (!out || !reqs || nreq < 1 || nreq > 65536) return BS_ERR_INVALID_ARG;
+    *out = nullptr;
+    bs_batch_opts o{};
+    o.use_graph = 1;
+    if (opts) o = *opts;
+    // validate and plan on the host
+    std::vector<BReq> h(nreq);
+    std::vector<uint32_t> unit0(nreq + 1, 0);
+    int device = -1;
+    size_t scratch = 0;
+    std::vector<size_t> bits_off(nreq, 0), cnt_off(nreq, 0), choff_off(nreq, 0);
+    auto take = [&](size_t bytes) {
+        size_t at = (scratch + 255) & ~(size_t)255;
+        scratch = at + bytes;
+        return at;
+    };
+    std::string mix;
+    uint64_t total_rows = 0;
+    int n_layout[3] = {0, 0, 0};
+    for (int r = 0; r < nreq; r++) {
+        const bs_request &q = reqs[r];
+        if (q.npreds < 1 || q.npreds > kMaxPreds || !q.preds[0].col) return BS_ERR_INVALID_ARG;
+        const bs_column *proj = q.proj ? q.proj : q.preds[0].col;
+        const Column &pc = proj->c;
+        if (pc.raw || !pc.d_arena) return BS_ERR_UNSUPPORTED;
+        if (q.out_cap && !q.d_out) return BS_ERR_INVALID_ARG;
+        if (device < 0) device = pc.device;
+        if (pc.device != device) return BS_ERR_INVALID_ARG;
+        BReq &R = h[r];
+        R = BReq{};
+        R.npred = q.npreds;
+        for (int p = 0; p < q.npreds; p++) {
+            const bs_column *col = q.preds[p].col;
+            if (!col || col->c.n != pc.n || col->c.device != device) return BS_ERR_INVALID_ARG;
+            if (col->c.raw || !col->c.d_arena) return BS_ERR_UNSUPPORTED;
+            if (q.preds[p].op < BS_LT || q.preds[p].op > BS_BETWEEN) return BS_ERR_INVALID_ARG;
+            KPred kp;
+            int rc = rewrite_literal(col->c, q.preds[p].op, q.preds[p].lit, q.preds[p].lit2, kp);
+            if (rc) return rc;
+            plan_scan(col->c, kp, nullptr, false, R.pred[p].a, R.pred[p].plan);
+            R.pred[p].a.out = nullptr;  // the batch kernel stores the final word itself
+            n_layout[col->c.layout]++;
+        }
+        R.look = make_look_args(pc);
+        R.kmax = kmax_for(R.look);
+        R.val1 = pc.d_val1;
+        R.look.out_vals = q.d_out;
+        R.look.out_cap = q.d_out ? q.out_cap : 0;
+        R.look.count = q.d_count;
+        R.n_chunks = R.look.n_chunks;
+        unit0[r] = (r ? unit0[r - 1] + h[r - 1].n_chunks : 0);
+        total_rows += pc.n;
+        const uint64_t nw = (pc.n + 31) / 32;
+        bits_off[r] = q.d_bits ? SIZE_MAX : take(std::max<uint64_t>(4, nw * 4));
+        cnt_off[r] = take(std::max<uint64_t>(4, (uint64_t)R.n_chunks * 4));
+        choff_off[r] = take(std::max<uint64_t>(8, (uint64_t)R.n_chunks * 8));
+    }
+    unit0[nreq] = unit0[nreq - 1] + h[nreq - 1].n_chunks;
+    const size_t o_ctr = take(256);
+    const size_t o_unit0 = take(unit0.size() * 4);
+    const size_t o_reqs = take(sizeof(BReq) * (size_t)nreq);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(device) != cudaSuccess) return BS_ERR_CUDA;
+    auto *b = new (std::nothrow) bs_batch;
+    if (!b) return BS_ERR_OOM;
+    b->device = device;
+    b->nreq = nreq;
+    b->use_graph = o.use_graph != 0;
+    int rc = BS_OK;
+    if (cudaMalloc(&b->d_arena, scratch) != cudaSuccess) {
+        cudaGetLastError();
+        rc = BS_ERR_OOM;
+    }
+    uint8_t *base = (uint8_t *)b->d_arena;
+    if (rc == BS_OK) {
+        uint32_t *status = status_word();
+        if (!status) rc = BS_ERR_CUDA;
+        for (int r = 0; r < nreq && rc == BS_OK; r++) {
+            BReq &R = h[r];
+            R.bits = reqs[r].d_bits ? reqs[r].d_bits : (uint32_t *)(base + bits_off[r]);
+            R.chunk_cnt = (uint32_t *)(base + cnt_off[r]);
+            R.chunk_off = (uint64_t *)(base + choff_off[r]);
+            R.unit0 = unit0[r];
+            R.look.bits = R.bits;
+            R.look.status = status;
+            for (int p = 0; p < R.npred; p++) R.pred[p].a.status = status;
+        }
+        b->k.reqs = (const BReq *)(base + o_reqs);
+        b->k.unit0 = (const uint32_t *)(base + o_unit0);
+        b->k.nreq = nreq;
+        b->k.total_units = unit0[nreq];
+        b->k.ctr = (uint32_t *)(base + o_ctr);
+        b->k.status = status;
+        if (rc == BS_OK && (cudaMemcpy(base + o_reqs, h.data(), sizeof(BReq) * (size_t)nreq, cudaMemcpyHostToDevice) !=
+                                cudaSuccess ||
+                            cudaMemcpy(base + o_unit0, unit0.data(), unit0.size() * 4, cudaMemcpyHostToDevice) !=
+                                cudaSuccess))
+            rc = BS_ERR_CUDA;
+    }
+    // launch shape: explicit, cached, autotuned or the default
+    int threads = o.threads > 0 ? o.threads : 256, bps = o.blocks_per_sm;
+    if (rc == BS_OK) {
+        cudaDeviceProp prop{};
+        cudaGetDeviceProperties(&prop, device);
+        char key[384];
+        std::snprintf(key, sizeof key, "%s|nreq=%d|rows=2^%d|vbs=%d,bsl=%d,bp=%d", prop.name, nreq,
+                      total_rows ? 63 - __builtin_clzll(total_rows) : 0, n_layout[BS_PPVBS], n_layout[BS_BYTESLICE],
+                      n_layout[BS_BITPACKED]);
+        const std::string path = tune_path(o);
+        if (o.threads <= 0 && !o.autotune) tune_lookup(path, key, threads, bps);
+        if (o.autotune) {
+            const int cand_t[3] = {128, 256, 512};
+            const int cand_b[3] = {1, 2, 0};
+            double best = 1e30;
+            int bt = 256, bb = 0;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (int ti = 0; ti < 3 && rc == BS_OK; ti++) {
+                for (int bi = 0; bi < 3 && rc == BS_OK; bi++) {
+                    if (shape(b, cand_t[ti], cand_b[bi]) != BS_OK) continue;
+                    if (launch_direct(b, nullptr) != BS_OK) { cudaGetLastError(); continue; }
+                    cudaEventRecord(e0, nullptr);
+                    for (int rep = 0; rep < 3; rep++) launch_direct(b, nullptr);
+                    cudaEventRecord(e1, nullptr);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = BS_ERR_CUDA; break; }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    const double us = ms * 1000.0 / 3;
+                    if (us < best) { best = us; bt = cand_t[ti]; bb = cand_b[bi]; }
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            threads = bt;
+            bps = bb;
+            if (rc == BS_OK) tune_store(path, key, bt, bb, best);
+        }
+        if (rc == BS_OK) rc = shape(b, threads, bps);
+        if (rc == BS_OK) rc = capture(b);
+    }
+    cudaSetDevice(prev);
+    if (rc != BS_OK) {
+        bs_batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return BS_OK;
+}
+
+int bs_batch_launch(bs_batch *b, void *stream) {
+    if (!b) return BS_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != b->device && cudaSetDevice(b->device) != cudaSuccess) return BS_ERR_CUDA;
+    int rc;
+    if (b->graph_ok) rc = cudaGraphLaunch(b->exec, (cudaStream_t)stream) == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+    else rc = launch_direct(b, (cudaStream_t)stream);
+    if (prev != b->device) cudaSetDevice(prev);
+    return rc;
+}
+
+int bs_batch_info(const bs_batch *b, int32_t *threads, int32_t *ctas, int32_t *graph) {
+    if (!b) return BS_ERR_INVALID_ARG;
+    if (threads) *threads = b->threads;
+    if (ctas) *ctas = b->ctas;
+    if (graph) *graph = b->graph_ok ? 1 : 0;
+    return BS_OK;
+}
+
+void bs_batch_free(bs_batch *b) {
+    if (!b) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->d_arena) cudaFree(b->d_arena);
+    cudaSetDevice(prev);
+    delete b;
+}
+
+}  // extern "C"

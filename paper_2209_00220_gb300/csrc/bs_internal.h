@@ -78,6 +78,7 @@ struct Column {
     std::vector<uint64_t> first_byte_rows;  // PP-VBS: rows whose code starts with byte b
     std::vector<int32_t> val2;    // PP-VBS decode: value of codes <= 2 bytes, by first two bytes
     std::vector<uint32_t> leaf2;  // PP-VBS decode: first dictionary index of a level-2 leaf
+    std::vector<int32_t> val1;    // PP-VBS decode: value of each one-byte code
 
     // host copy of the device layout (kept for host_only / keep_host)
     bool has_host = false;
@@ -98,6 +99,7 @@ struct Column {
     const uint8_t *d_deep[kMaxCodeBytes + 1] = {nullptr};
     const uint32_t *d_packed = nullptr;
     const int32_t *d_val2 = nullptr;
+    const int32_t *d_val1 = nullptr;  // PP-VBS: value of each one-byte code (256 entries)
     const uint32_t *d_leaf2 = nullptr;
     const int32_t *d_dict = nullptr;
     uint64_t dict_size() const { return dict.size(); }

@@ -91,7 +91,7 @@ void free_device(Column &c) {
 
 int upload_column(Column &c) {
     Arena ar;
-    size_t o_dense = 0, o_packed = 0, o_val2 = 0, o_leaf2 = 0, o_dict = 0;
+    size_t o_dense = 0, o_packed = 0, o_val2 = 0, o_leaf2 = 0, o_val1 = 0, o_dict = 0;
     size_t o_mask[kMaxCodeBytes + 1] = {0}, o_off[kMaxCodeBytes + 1] = {0}, o_deep[kMaxCodeBytes + 1] = {0};
     if (c.layout == BS_PPVBS || c.layout == BS_BYTESLICE) o_dense = ar.take(c.h_dense.size() + 16);
     if (c.layout == BS_PPVBS) {
@@ -102,6 +102,7 @@ int upload_column(Column &c) {
         }
         o_val2 = ar.take(c.val2.size() * 4 + 4);
         o_leaf2 = ar.take(c.leaf2.size() * 4 + 4);
+        o_val1 = ar.take(c.val1.size() * 4 + 4);
     }
     if (c.layout == BS_BITPACKED) o_packed = ar.take(c.h_packed.size() * 4);
     o_dict = ar.take(c.dict.size() * 4 + 4);
@@ -140,6 +141,8 @@ int upload_column(Column &c) {
         ok = ok && put(o_leaf2, c.leaf2.data(), c.leaf2.size() * 4);
         c.d_val2 = (const int32_t *)(b + o_val2);
         c.d_leaf2 = (const uint32_t *)(b + o_leaf2);
+        ok = ok && put(o_val1, c.val1.data(), c.val1.size() * 4);
+        c.d_val1 = (const int32_t *)(b + o_val1);
     }
     if (c.layout == BS_BITPACKED) {
         ok = ok && put(o_packed, c.h_packed.data(), c.h_packed.size() * 4);

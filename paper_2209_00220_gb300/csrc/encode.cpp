@@ -284,11 +284,13 @@ static void ppe_numerical(const std::vector<uint64_t> &Q, std::vector<uint64_t> 
 static void build_decode_tables(Column &c) {
     c.val2.assign(65536, 0);
     c.leaf2.assign(65536, 0);
+    c.val1.assign(256, 0);
     for (size_t i = 0; i < c.dict.size(); i++) {
         const uint64_t C = c.dcode[i];
         const int L = c.dlen[i];
         if (L == 1) {
             c.val2[(size_t)(C << 8)] = c.dict[i];
+            c.val1[(size_t)C] = c.dict[i];
         } else if (L == 2) {
             c.val2[(size_t)C] = c.dict[i];
         } else {

@@ -1,0 +1,600 @@
+// Device code of the lookup kernels for sm_103a (shared by lookup.cu and
+// batch.cu) (Algorithm 4 and the lookups of Sections 2.3 and
+// 2.5): result bit vector -> values of the selected rows in ascending row
+// order, or zero-padded codes.
+//
+// Algorithm 4 walks the bit vector word by word with running slice indices
+// I_j. On the GPU the output position of every selected row comes from three
+// kernels instead:
+//   1. count:  one warp per chunk of 16 tiles (16K rows) popcounts its 2 KB of
+//              the bit vector with 16-byte loads; each CTA (8 chunks) also
+//              writes the total of its 8 chunks;
+//   2. scan:   one CTA turns the CTA totals into exclusive offsets (coalesced
+//              segments of 4096) and writes the selected-row count;
+//   3. gather: one CTA per chunk; its offset is its CTA offset plus the counts
+//              of the chunks before it in the same group of 8. Per tile, a warp
+//              prefix-sums its 32 word popcounts, lists the selected rows in
+//              shared memory (ascending), and lanes take list entries
+//              round-robin, four at a time, so output writes are coalesced and
+//              many loads are in flight.
+//
+// For PP-VBS a warp loads, per level j, the mask words M_j of the 256-row
+// groups whose selected rows have byte j-1 (the paper's per-block beta test)
+// and prefix-sums their popcounts into shared memory; a selected row's length
+// and the address of each of its bytes then come from shared memory alone, so
+// all its byte loads are issued together. A tile with many selected rows first
+// copies its 1 KB of BS_1 into shared memory with coalesced 16-byte loads.
+// Codes of at most two bytes decode with one table load (value by first two
+// bytes); longer codes sit in level-2 leaves whose values have consecutive
+// dictionary indices, decoded as dict[leaf start + rest - 1].
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dev_common.cuh"
+#include "kernels.h"
+
+namespace bs {
+namespace {
+
+
+constexpr int kChunkTiles = 16;
+constexpr int kLookupThreads = 256;
+constexpr int kLookupWarps = kLookupThreads / 32;
+constexpr int kTilesPerWarp = kChunkTiles / kLookupWarps;
+constexpr int kUnroll = 4;
+constexpr int kGroupChunks = 8;       // chunks counted by one CTA of the count kernel
+constexpr int kScanBlock = 1024;
+constexpr uint32_t kStageMin = 64;    // selected rows from which a tile stages BS_1
+constexpr uint32_t kSparseMax = 256;  // selected rows up to which a chunk is resolved row-parallel
+
+struct LookK {
+    int32_t layout;
+    int32_t K;            // PP-VBS longest code / ByteSlice slices
+    int32_t k;            // code bits (ByteSlice / Bit-Packed)
+    int32_t identity;
+    int64_t domain_min;
+    uint64_t n;
+    uint32_t n_tiles;
+    uint32_t n_chunks;
+    const uint8_t *dense;
+    uint64_t slice_bytes;
+    const uint32_t *mask[kMaxCodeBytes + 1];
+    const uint32_t *off[kMaxCodeBytes + 1];
+    const uint8_t *deep[kMaxCodeBytes + 1];
+    uint64_t deep_len[kMaxCodeBytes + 1];
+    const uint32_t *packed;
+    const int32_t *val2;
+    const uint32_t *leaf2;
+    const int32_t *dict;
+    uint64_t dict_size;
+    const uint32_t *bits;
+    int32_t bits_vec;     // bits is 16-byte aligned
+    uint32_t n_groups;    // groups of kGroupChunks chunks
+    uint32_t *chunk_cnt;  // workspace: count per chunk
+    uint64_t *group_off;  // workspace: total per group, then exclusive offset
+    int32_t *out_vals;
+    uint64_t *out_codes;
+    uint64_t out_cap;
+    uint64_t *count;
+    uint32_t *status;
+};
+
+
+__device__ __forceinline__ uint32_t tile_pos(uint32_t q) {
+    const uint32_t lane = q >> 5, r = q & 31u, b = r >> 3, w = r & 7u;
+    return (w >> 2) * 512u + lane * 16u + (w & 3u) * 4u + b;
+}
+
+// A lane's 32 slice bytes arrive as words x0..x7 with word w byte b = row
+// 8b + w; two 4x4 byte transposes put them in row order (word k = rows
+// 4k..4k+3): rows 8m..8m+3 are byte m of x0..x3, rows 8m+4..8m+7 byte m of
+// x4..x7.
+__device__ __forceinline__ void transpose4(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t &y0,
+                                           uint32_t &y1, uint32_t &y2, uint32_t &y3) {
+    const uint32_t t0 = __byte_perm(a, b, 0x5140), t1 = __byte_perm(a, b, 0x7362);
+    const uint32_t t2 = __byte_perm(c, d, 0x5140), t3 = __byte_perm(c, d, 0x7362);
+    y0 = __byte_perm(t0, t2, 0x5410);
+    y1 = __byte_perm(t0, t2, 0x7632);
+    y2 = __byte_perm(t1, t3, 0x5410);
+    y3 = __byte_perm(t1, t3, 0x7632);
+}
+
+__device__ __forceinline__ void transpose_lane_bytes(const uint4 &v0, const uint4 &v1, uint4 &r0, uint4 &r1) {
+    uint32_t e0, e1, e2, e3, o0, o1, o2, o3;  // even / odd row-order words
+    transpose4(v0.x, v0.y, v0.z, v0.w, e0, e1, e2, e3);
+    transpose4(v1.x, v1.y, v1.z, v1.w, o0, o1, o2, o3);
+    r0 = make_uint4(e0, o0, e1, o1);
+    r1 = make_uint4(e2, o2, e3, o3);
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+    return v;
+}
+
+__device__ __forceinline__ int32_t dict_value(const LookK &a, uint64_t idx) {
+    if (idx >= a.dict_size) {
+        atomicOr(a.status, kStatusBounds);
+        return 0;
+    }
+    return __ldg(a.dict + idx);
+}
+
+// Value of a code: PP-VBS via the two-byte tables, the others by rank or range.
+template <int LAYOUT>
+__device__ __forceinline__ int32_t decode_value(const LookK &a, uint64_t code, int len) {
+    if (LAYOUT == BS_PPVBS) {
+        const uint32_t c1 = (uint32_t)(code >> (8 * (len - 1))) & 0xFFu;
+        const uint32_t c2 = len >= 2 ? (uint32_t)(code >> (8 * (len - 2))) & 0xFFu : 0u;
+        const uint32_t key = (c1 << 8) | c2;
+        if (len <= 2) return __ldg(a.val2 + key);
+        const uint64_t rest = code & ((1ull << (8 * (len - 2))) - 1);
+        return dict_value(a, (uint64_t)__ldg(a.leaf2 + key) + rest - 1);
+    }
+    if (a.identity) return (int32_t)((int64_t)code + a.domain_min);
+    return dict_value(a, code);
+}
+
+// 16-byte aligned: dense[] receives 16-byte vector stores, one struct per warp
+template <int KMAX>
+struct __align__(16) WarpSmemT {
+    uint8_t dense[kTileRows];         // staged BS_1 of the tile
+    uint32_t seg[KMAX <= 4 ? kTileRows / 4 + 4 : 4];  // staged BS_2 segment (dense path, KMAX <= 4)
+    uint16_t list[kTileRows];         // sparse path: selected rows; dense path: decode keys
+    uint32_t skip[kTileWords];        // dense path: entries already written
+    uint32_t mask[KMAX + 1][kTileWords];
+    uint32_t pref[KMAX + 1][kTileWords];
+};
+
+static_assert(sizeof(WarpSmemT<2>) % 16 == 0 && sizeof(WarpSmemT<4>) % 16 == 0 && sizeof(WarpSmemT<8>) % 16 == 0,
+              "per-warp shared memory must keep 16-byte alignment");
+
+// Code (unpadded) and length of tile-local row q of tile t. PP-VBS reads the
+// warp's per-level mask words and BS_j prefixes from sm, and BS_1 from sm.dense
+// when the tile was staged. KMAX bounds the code length (template constant).
+template <int LAYOUT, int KMAX>
+__device__ __forceinline__ void fetch_code(const LookK &a, uint64_t t, uint32_t q, int levels,
+                                           const WarpSmemT<KMAX> *sm,
+                                           bool staged, uint64_t &code, int &len) {
+    if (LAYOUT == BS_PPVBS) {
+        const uint32_t wq = q >> 5, bq = q & 31u, below = (1u << bq) - 1u;
+        len = 1;
+#pragma unroll
+        for (int j = 2; j <= KMAX; j++)
+            if (j <= levels && len == j - 1 && ((sm->mask[j][wq] >> bq) & 1u)) len = j;
+        uint32_t b[KMAX + 1];
+        b[1] = staged ? (uint32_t)sm->dense[q] : (uint32_t)__ldg(a.dense + t * kTileRows + tile_pos(q));
+#pragma unroll
+        for (int j = 2; j <= KMAX; j++) {
+            b[j] = 0;
+            if (j <= len) {
+                const uint64_t idx = (uint64_t)sm->pref[j][wq] + __popc(sm->mask[j][wq] & below);
+                if (idx < a.deep_len[j]) b[j] = __ldg(a.deep[j] + idx);
+                else atomicOr(a.status, kStatusBounds);
+            }
+        }
+        code = b[1];
+#pragma unroll
+        for (int j = 2; j <= KMAX; j++)
+            if (j <= len) code = (code << 8) | b[j];
+    } else if (LAYOUT == BS_BYTESLICE) {
+        const uint64_t pos = t * kTileRows + tile_pos(q);
+        uint32_t b[KMAX];
+#pragma unroll
+        for (int s = 0; s < KMAX; s++) b[s] = s < a.K ? __ldg(a.dense + (uint64_t)s * a.slice_bytes + pos) : 0u;
+        uint64_t aligned = 0;
+#pragma unroll
+        for (int s = 0; s < KMAX; s++)
+            if (s < a.K) aligned = (aligned << 8) | b[s];
+        code = aligned >> (8 * a.K - a.k);
+        len = a.K;
+    } else {
+        const uint64_t bit = (t * kTileRows + q) * (uint64_t)a.k;
+        const uint32_t *p = a.packed + (bit >> 5);
+        const uint32_t lo = __ldg(p), hi = __ldg(p + 1);
+        code = __funnelshift_r(lo, hi, (uint32_t)(bit & 31u)) & (a.k == 32 ? kFull : ((1u << a.k) - 1u));
+        len = (a.k + 7) / 8;
+    }
+}
+
+// Dense PP-VBS tile: BS_1 and the tile's BS_2 segment are staged in shared
+// memory; each lane walks its own selected rows in order and leaves a 16-bit
+// decode key (first two code bytes) per output slot, codes of three or more
+// bytes being decoded on the spot; the warp then decodes the keys and writes
+// the values with coalesced stores.
+template <int KMAX>
+__device__ __forceinline__ void gather_dense_vbs(const LookK &a, uint64_t t, uint32_t sel, uint32_t excl,
+                                                 uint32_t total, int levels, uint64_t out_base, WarpSmemT<KMAX> &sm,
+                                                 const int32_t *val1, uint32_t lane) {
+    uint32_t seg_lo = 0;
+    if (levels >= 2) {
+        // BS_2 bytes of this tile are contiguous: [off_2[first group], off_2[first group of next tile])
+        seg_lo = __ldg(a.off[2] + t * kGroupsPerTile);
+        const uint32_t seg_hi = __ldg(a.off[2] + t * kGroupsPerTile + kGroupsPerTile);
+        const uint32_t w0 = seg_lo >> 2, w1 = (seg_hi + 3) >> 2;
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(a.deep[2]);
+        constexpr uint32_t kSegWords = sizeof(sm.seg) / 4;
+        for (uint32_t i = lane; i < w1 - w0 && i < kSegWords; i += 32) sm.seg[i] = __ldg(src + w0 + i);
+    }
+    sm.skip[lane] = 0u;
+    __syncwarp();
+    const uint8_t *seg = reinterpret_cast<const uint8_t *>(sm.seg) + (seg_lo & 3u);
+    const uint32_t m2 = levels >= 2 ? sm.mask[2][lane] : 0u;
+    const uint32_t p2 = levels >= 2 ? sm.pref[2][lane] - seg_lo : 0u;
+    const uint32_t m3 = (KMAX >= 3 && levels >= 3) ? sm.mask[KMAX >= 3 ? 3 : 2][lane] : 0u;
+    uint32_t pos = excl, r = sel;
+    while (r) {
+        const uint32_t b = __ffs(r) - 1, below = (1u << b) - 1u;
+        r &= r - 1;
+        const uint32_t q = lane * 32u + b;
+        const uint32_t c1 = sm.dense[q];
+        uint32_t key = c1 << 8;
+        if ((m2 >> b) & 1u) {
+            key |= seg[p2 + __popc(m2 & below)];
+            if (KMAX >= 3 && ((m3 >> b) & 1u)) {  // three or more bytes: decode now
+                uint64_t code;
+                int len;
+                fetch_code<BS_PPVBS, KMAX>(a, t, q, levels, &sm, true, code, len);
+                const uint64_t o = out_base + pos;
+                if (o < a.out_cap) a.out_vals[o] = decode_value<BS_PPVBS>(a, code, len);
+                atomicOr(&sm.skip[pos >> 5], 1u << (pos & 31));
+            }
+        }
+        sm.list[pos++] = (uint16_t)key;
+    }
+    __syncwarp();
+    for (uint32_t i0 = 0; i0 < total; i0 += 32 * kUnroll) {
+        int32_t v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+            v[u] = 0;
+            if (i < total) {
+                const uint32_t key = sm.list[i];
+                v[u] = (key & 0xFFu) ? __ldg(a.val2 + key) : val1[key >> 8];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+            const uint64_t o = out_base + i;
+            if (i < total && o < a.out_cap && !((sm.skip[i >> 5] >> (i & 31)) & 1u)) a.out_vals[o] = v[u];
+        }
+    }
+    __syncwarp();
+}
+
+template <int LAYOUT, bool CODES, int KMAX>
+__device__ __forceinline__ void gather_tile(const LookK &a, uint64_t t, uint32_t sel, uint64_t out_base,
+                                            WarpSmemT<KMAX> &sm, const int32_t *val1, uint32_t lane) {
+    const uint32_t cnt = __popc(sel);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, d);
+        if (lane >= (uint32_t)d) incl += v;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
+    constexpr bool kDenseOk = LAYOUT == BS_PPVBS && !CODES && KMAX <= 4;
+    const bool dense = kDenseOk && total >= kStageMin;
+    if (!dense) {
+        uint32_t pos = incl - cnt, r = sel;
+        while (r) {
+            const uint32_t b = __ffs(r) - 1;
+            r &= r - 1;
+            sm.list[pos++] = (uint16_t)(lane * 32u + b);
+        }
+    }
+    // a dense tile copies its BS_1 bytes once, coalesced, instead of one load
+    // per row, and stores them in plain row order (byte of row q at dense[q])
+    const bool staged = LAYOUT == BS_PPVBS && total >= kStageMin;
+    if (staged) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.dense + t * kTileRows);
+        const uint4 v0 = __ldg(src + lane), v1 = __ldg(src + 32 + lane);
+        uint4 r0, r1;
+        transpose_lane_bytes(v0, v1, r0, r1);
+        uint4 *dst = reinterpret_cast<uint4 *>(sm.dense + lane * 32u);
+        dst[0] = r0;
+        dst[1] = r1;
+    }
+    int levels = 1;
+    if (LAYOUT == BS_PPVBS) {
+        const uint64_t w = t * kTileWords + lane;
+        uint32_t reach = sel;  // selected rows that have byte j-1
+        for (int j = 2; j <= min(a.K, KMAX); j++) {
+            const uint32_t bal = __ballot_sync(kFull, reach != 0u);
+            if (!bal) break;
+            const uint32_t gact = (bal >> (lane & 24u)) & 0xFFu;
+            const uint32_t m = gact ? __ldg(a.mask[j] + w) : 0u;
+            const uint32_t c = __popc(m);
+            uint32_t inc = c;
+#pragma unroll
+            for (int d = 1; d < 8; d <<= 1) {
+                const uint32_t v = __shfl_up_sync(kFull, inc, d);
+                if ((lane & 7u) >= (uint32_t)d) inc += v;
+            }
+            const uint32_t goff = gact ? __ldg(a.off[j] + t * kGroupsPerTile + (lane >> 3)) : 0u;
+            sm.mask[j][lane] = m;
+            sm.pref[j][lane] = goff + inc - c;
+            reach = sel & m;
+            levels = j;
+        }
+    }
+    __syncwarp();
+    if (kDenseOk && dense) {
+        gather_dense_vbs<KMAX>(a, t, sel, incl - cnt, total, levels, out_base, sm, val1, lane);
+        return;
+    }
+    for (uint32_t i0 = 0; i0 < total; i0 += 32 * kUnroll) {
+        uint64_t code[kUnroll];
+        int len[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+            code[u] = 0;
+            len[u] = 1;
+            if (i < total) fetch_code<LAYOUT, KMAX>(a, t, sm.list[i], levels, &sm, staged, code[u], len[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+            const uint64_t o = out_base + i;
+            if (i < total && o < a.out_cap) {
+                if (CODES) a.out_codes[o] = LAYOUT == BS_PPVBS ? (code[u] << (8 * (a.K - len[u]))) : code[u];
+                else a.out_vals[o] = decode_value<LAYOUT>(a, code[u], len[u]);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Code of one row with no shared-memory help: PP-VBS finds byte j at
+// off_j[group] + popcounts of the group's earlier mask words + rank in its word
+// (all within one 32-byte sector of M_j).
+template <int LAYOUT, int KMAX>
+__device__ __forceinline__ void row_code(const LookK &a, uint64_t row, uint64_t &code, int &len) {
+    const uint64_t t = row >> 10;
+    const uint32_t q = (uint32_t)(row & 1023u);
+    if (LAYOUT == BS_PPVBS) {
+        code = __ldg(a.dense + t * kTileRows + tile_pos(q));
+        len = 1;
+        const uint64_t g = row >> 8, w = row >> 5;
+        const uint32_t b = (uint32_t)(row & 31u), below = (1u << b) - 1u;
+        for (int j = 2; j <= min(a.K, KMAX); j++) {
+            const uint32_t mw = __ldg(a.mask[j] + w);
+            if (!((mw >> b) & 1u)) break;
+            uint64_t idx = __ldg(a.off[j] + g) + __popc(mw & below);
+            for (uint64_t x = g * kGroupWords; x < w; x++) idx += __popc(__ldg(a.mask[j] + x));
+            uint32_t byte = 0;
+            if (idx < a.deep_len[j]) byte = __ldg(a.deep[j] + idx);
+            else atomicOr(a.status, kStatusBounds);
+            code = (code << 8) | byte;
+            len = j;
+        }
+    } else {
+        fetch_code<LAYOUT, KMAX>(a, t, q, 1, (const WarpSmemT<KMAX> *)nullptr, false, code, len);
+    }
+}
+
+// Dense PP-VBS tile whose codes have at most two bytes: every load that does
+// not depend on another (the lane's 32 BS_1 bytes, its M_2 word, its group's
+// BS_2 offset and the tile's BS_2 segment bounds) is issued in one round; the
+// segment words and then the two-byte decode table follow. Each lane walks its
+// own selected rows in order and leaves a 16-bit key (first two code bytes) per
+// output slot; the warp then decodes the keys and stores them coalesced.
+__device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint32_t sel, uint64_t out_base,
+                                                WarpSmemT<2> &sm, const int32_t *val1, uint32_t lane) {
+    // round 1: independent loads
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.dense + t * kTileRows);
+    const uint4 v0 = __ldg(src + lane), v1 = __ldg(src + 32 + lane);
+    const bool has2 = a.K >= 2;
+    const uint32_t m2 = has2 ? __ldg(a.mask[2] + t * kTileWords + lane) : 0u;
+    const uint32_t goff = has2 ? __ldg(a.off[2] + t * kGroupsPerTile + (lane >> 3)) : 0u;
+    const uint32_t seg_lo = has2 ? __ldg(a.off[2] + t * kGroupsPerTile) : 0u;
+    const uint32_t seg_hi = has2 ? __ldg(a.off[2] + t * kGroupsPerTile + kGroupsPerTile) : 0u;
+    // ALU while they fly: output positions of this lane's rows
+    const uint32_t cnt = __popc(sel);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, d);
+        if (lane >= (uint32_t)d) incl += v;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t c2 = __popc(m2);
+    uint32_t inc2 = c2;
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, inc2, d);
+        if ((lane & 7u) >= (uint32_t)d) inc2 += v;
+    }
+    // round 2: the tile's BS_2 bytes (contiguous)
+    if (has2) {
+        const uint32_t w0 = seg_lo >> 2, w1 = (seg_hi + 3) >> 2;
+        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(a.deep[2]);
+        constexpr uint32_t kSegWords = sizeof(sm.seg) / 4;
+        for (uint32_t i = lane; i < w1 - w0 && i < kSegWords; i += 32) sm.seg[i] = __ldg(s32 + w0 + i);
+    }
+    uint4 r0, r1;
+    transpose_lane_bytes(v0, v1, r0, r1);
+    uint4 *dst = reinterpret_cast<uint4 *>(sm.dense + lane * 32u);
+    dst[0] = r0;
+    dst[1] = r1;
+    __syncwarp();
+    const uint8_t *seg = reinterpret_cast<const uint8_t *>(sm.seg) + (seg_lo & 3u);
+    const uint32_t p2 = goff + inc2 - c2 - seg_lo;  // lane's first BS_2 byte, relative to the segment
+    uint32_t pos = incl - cnt, r = sel;
+    while (r) {
+        const uint32_t b = __ffs(r) - 1;
+        r &= r - 1;
+        uint32_t key = (uint32_t)sm.dense[lane * 32u + b] << 8;
+        if ((m2 >> b) & 1u) key |= seg[p2 + __popc(m2 & ((1u << b) - 1u))];
+        sm.list[pos++] = (uint16_t)key;
+    }
+    __syncwarp();
+    // round 3: decode and store
+    for (uint32_t i0 = 0; i0 < total; i0 += 32 * kUnroll) {
+        int32_t v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+            v[u] = 0;
+            if (i < total) {
+                const uint32_t key = sm.list[i];
+                v[u] = (key & 0xFFu) ? __ldg(a.val2 + key) : val1[key >> 8];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+            const uint64_t o = out_base + i;
+            if (i < total && o < a.out_cap) a.out_vals[o] = v[u];
+        }
+    }
+    __syncwarp();
+}
+
+// One warp resolves chunk c (16 tiles) whose first output slot is `base`.
+// It reads the chunk's 512 bit vector words at once. A sparse chunk (at most
+// kSparseMax selected rows) lists its rows in shared memory and resolves them
+// all in parallel across lanes; a dense chunk goes tile by tile.
+template <int LAYOUT, bool CODES, int KMAX>
+__device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_t base, WarpSmemT<KMAX> &sm,
+                                             const int32_t *val1, uint32_t lane) {
+    const uint64_t nwords = (a.n + 31) / 32;
+    // the chunk's words: block i (4 tiles) holds words i*128 + 4L + 0..3 at lane L
+    const uint64_t w0 = (uint64_t)c * kChunkTiles * kTileWords;
+    uint32_t wv[4][4];
+    uint32_t cnt[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        cnt[i] = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint64_t w = w0 + (uint64_t)(i * 128 + 4 * lane + k);
+            const uint32_t vm = w < nwords ? valid_mask(w * 32u, a.n) : 0u;
+            wv[i][k] = vm ? (__ldg(a.bits + w) & vm) : 0u;
+            cnt[i] += __popc(wv[i][k]);
+        }
+    }
+    const uint32_t chunk_total = warp_sum(cnt[0] + cnt[1] + cnt[2] + cnt[3]);
+    if (chunk_total == 0) return;
+    if (chunk_total <= kSparseMax) {
+        // list the selected rows (row offset inside the chunk) in row order
+        uint32_t pos0 = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            uint32_t incl = cnt[i];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t v = __shfl_up_sync(kFull, incl, d);
+                if (lane >= (uint32_t)d) incl += v;
+            }
+            uint32_t pos = pos0 + incl - cnt[i];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                uint32_t r = wv[i][k];
+                while (r) {
+                    const uint32_t b = __ffs(r) - 1;
+                    r &= r - 1;
+                    sm.list[pos++] = (uint16_t)((i * 128 + 4 * lane + k) * 32 + b);
+                }
+            }
+            pos0 += __shfl_sync(kFull, incl, 31);
+        }
+        __syncwarp();
+        const uint64_t row0 = (uint64_t)c * kChunkTiles * kTileRows;
+        for (uint32_t i0 = 0; i0 < chunk_total; i0 += 32 * kUnroll) {
+            uint64_t code[kUnroll];
+            int len[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+                code[u] = 0;
+                len[u] = 1;
+                if (i < chunk_total) row_code<LAYOUT, KMAX>(a, row0 + sm.list[i], code[u], len[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+                const uint64_t o = base + i;
+                if (i < chunk_total && o < a.out_cap) {
+                    if (CODES) a.out_codes[o] = LAYOUT == BS_PPVBS ? (code[u] << (8 * (a.K - len[u]))) : code[u];
+                    else if (LAYOUT == BS_PPVBS && len[u] == 1) a.out_vals[o] = val1[code[u] & 0xFFu];
+                    else a.out_vals[o] = decode_value<LAYOUT>(a, code[u], len[u]);
+                }
+            }
+        }
+        __syncwarp();
+        return;
+    }
+    // dense chunk: tile by tile (tile 4i + j is lanes 8j..8j+7 of block i)
+    uint32_t tcnt[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        uint32_t v = cnt[i];
+        v += __shfl_xor_sync(kFull, v, 1);
+        v += __shfl_xor_sync(kFull, v, 2);
+        v += __shfl_xor_sync(kFull, v, 4);
+        tcnt[i] = v;  // count of tile 4i + (lane >> 3)
+    }
+    for (int tt = 0; tt < kChunkTiles; tt++) {
+        const uint32_t tc = __shfl_sync(kFull, tcnt[tt >> 2], (tt & 3) * 8);
+        const uint64_t t = (uint64_t)c * kChunkTiles + tt;
+        if (tc && t < a.n_tiles && base < a.out_cap) {
+            const uint64_t w = t * kTileWords + lane;
+            const uint32_t vm = valid_mask(w * 32u, a.n);
+            const uint32_t sel = vm ? (__ldg(a.bits + w) & vm) : 0u;
+            if (LAYOUT == BS_PPVBS && !CODES && KMAX == 2 && tc >= kStageMin)
+                gather_dense_k2(a, t, sel, base, reinterpret_cast<WarpSmemT<2> &>(sm), val1, lane);
+            else
+                gather_tile<LAYOUT, CODES, KMAX>(a, t, sel, base, sm, val1, lane);
+        }
+        base += tc;
+    }
+}
+
+// LookK view of a column (the per-call fields are filled by the caller).
+inline LookK make_look_args(const Column &c) {
+    LookK a{};
+    a.layout = c.layout;
+    a.K = c.layout == BS_PPVBS ? c.K : c.S;
+    a.k = c.k;
+    a.identity = c.identity ? 1 : 0;
+    a.domain_min = c.domain_min;
+    a.n = c.n;
+    a.n_tiles = c.n_tiles;
+    a.n_chunks = (c.n_tiles + kChunkTiles - 1) / kChunkTiles;
+    a.n_groups = (a.n_chunks + kGroupChunks - 1) / kGroupChunks;
+    a.dense = c.d_dense;
+    a.slice_bytes = c.dense_slice_bytes();
+    for (int j = 2; j <= c.K && c.layout == BS_PPVBS; j++) {
+        a.mask[j] = c.d_mask[j];
+        a.off[j] = c.d_off[j];
+        a.deep[j] = c.d_deep[j];
+        a.deep_len[j] = c.deep_len[j];
+    }
+    a.packed = c.d_packed;
+    a.val2 = c.d_val2;
+    a.leaf2 = c.d_leaf2;
+    a.dict = c.d_dict;
+    a.dict_size = c.dict.size();
+    return a;
+}
+
+// Largest code length the gather must handle, as a template constant.
+inline int kmax_for(const LookK &a) { return (a.layout == BS_PPVBS && a.K > 4) ? 8 : (a.K > 2 ? 4 : 2); }
+
+}  // namespace
+}  // namespace bs
