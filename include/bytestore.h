@@ -326,6 +326,89 @@ int bs_batch_info(const bs_batch *b, int32_t *threads, int32_t *ctas, int32_t *g
 
 void bs_batch_free(bs_batch *b);
 
+/* ------------------------------------------------------------- serving */
+
+/* Upper bound of the rows a predicate selects, from the dictionary counts
+ * (exact for PP-VBS and for dictionary-coded ByteSlice / Bit-Packed columns;
+ * the row count for columns coded by a declared value range). */
+int bs_estimate_rows(const bs_column *col, bs_op op, int32_t lit, int32_t lit2, uint64_t *out);
+
+/* A query for the server: a conjunction of 1..BS_MAX_CONJ predicates over
+ * equal-length resident columns, then the lookup of `proj` (NULL = the first
+ * predicate's column). */
+typedef struct {
+    int32_t npreds;
+    int32_t reserved;
+    bs_pred preds[BS_MAX_CONJ];
+    const bs_column *proj;
+} bs_query;
+
+/* Server options (NULL or 0 fields = defaults).
+ *   max_batch: queries per launch (64); slots: batches in flight on separate
+ *   streams (2); result_bytes: device memory for result buffers, the admission
+ *   cap (1 GiB); scratch_bytes: device memory for the bit vectors and chunk
+ *   offsets of queries in flight (4 GiB); threads: batch kernel CTA size (256);
+ *   device: CUDA device, -1 = current. */
+typedef struct {
+    int32_t max_batch;
+    int32_t slots;
+    uint64_t result_bytes;
+    uint64_t scratch_bytes;
+    int32_t threads;
+    int32_t device;
+} bs_server_opts;
+
+typedef struct {
+    int32_t status;           /* BS_OK, or BS_ERR_NOT_READY while queued or running */
+    int32_t reserved;
+    uint64_t count;           /* selected rows */
+    const int32_t *d_values;  /* device values, ascending row order; valid until bs_server_release */
+    double queue_us;          /* submission -> launch */
+    double latency_us;        /* submission -> results complete on the device (event observed) */
+} bs_query_result;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, batches;
+    double mean_batch;
+    uint64_t result_bytes_in_use, scratch_bytes_in_use;
+    uint64_t queued;
+} bs_server_stats;
+
+typedef struct bs_server bs_server; /* opaque */
+
+/* A serving loop over resident columns (the paper has no counterpart). A
+ * dispatcher thread admits queued queries in arrival order while their result
+ * buffers (bound from bs_estimate_rows) and scratch fit the budgets, packs the
+ * admitted ones into a batch and launches it (the batched kernel of
+ * bs_batch_create, sized to share the GPU with the other slots) as soon as a
+ * slot is free; queries arriving meanwhile join the next batch (continuous
+ * batching). Results stay in device memory until released. */
+int bs_server_create(const bs_server_opts *opts, bs_server **out);
+
+/* Enqueue a query (non-blocking). Errors: INVALID_ARG, UNSUPPORTED, CAPACITY
+ * (the query can never fit the server's memory budgets). */
+int bs_server_submit(bs_server *s, const bs_query *q, uint64_t *ticket);
+
+/* Result of a ticket: BS_ERR_NOT_READY until it completes. */
+int bs_server_poll(bs_server *s, uint64_t ticket, bs_query_result *res);
+
+/* Wait at most timeout_ms for a ticket (BS_ERR_TIMEOUT after that). */
+int bs_server_wait(bs_server *s, uint64_t ticket, int32_t timeout_ms, bs_query_result *res);
+
+/* Copy the first min(count, cap) values of a completed query to dst (device
+ * memory or pinned host memory), ordered on `stream`. Returns the number of
+ * values copied in *copied (may be NULL). NOT_READY if the query is not done. */
+int bs_server_copy_result(bs_server *s, uint64_t ticket, int32_t *dst, uint64_t cap, uint64_t *copied,
+                          void *stream);
+
+/* Free a completed query's result buffer (its d_values become invalid). */
+int bs_server_release(bs_server *s, uint64_t ticket);
+
+int bs_server_get_stats(const bs_server *s, bs_server_stats *st);
+
+/* Stops the dispatcher after the batches in flight finish, frees everything. */
+void bs_server_destroy(bs_server *s);
+
 /* -------------------------------------------------------- diagnostics */
 
 const char *bs_strerror(int status);

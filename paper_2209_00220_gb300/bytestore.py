@@ -64,6 +64,26 @@ class bs_batch_opts(ctypes.Structure):
                 ("tune_cache", ctypes.c_char_p)]
 
 
+class bs_query(ctypes.Structure):
+    _fields_ = [("npreds", _i32), ("reserved", _i32), ("preds", bs_pred * 4), ("proj", _vp)]
+
+
+class bs_server_opts(ctypes.Structure):
+    _fields_ = [("max_batch", _i32), ("slots", _i32), ("result_bytes", _u64), ("scratch_bytes", _u64),
+                ("threads", _i32), ("device", _i32)]
+
+
+class bs_query_result(ctypes.Structure):
+    _fields_ = [("status", _i32), ("reserved", _i32), ("count", _u64), ("d_values", _vp),
+                ("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double)]
+
+
+class bs_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", _u64), ("completed", _u64), ("rejected", _u64), ("batches", _u64),
+                ("mean_batch", ctypes.c_double), ("result_bytes_in_use", _u64), ("scratch_bytes_in_use", _u64),
+                ("queued", _u64)]
+
+
 class bs_advice(ctypes.Structure):
     _fields_ = [("layout", _i32), ("n_points", _i32), ("auc_byteslice", ctypes.c_double),
                 ("auc_ppvbs", ctypes.c_double), ("selectivity", ctypes.c_double * 100),
@@ -93,6 +113,15 @@ _SIGS = {
     "bs_batch_launch": ([_vp, _vp], _i32),
     "bs_batch_info": ([_vp, _vp, _vp, _vp], _i32),
     "bs_batch_free": ([_vp], None),
+    "bs_estimate_rows": ([_vp, _i32, _i32, _i32, _vp], _i32),
+    "bs_server_create": ([_vp, _vp], _i32),
+    "bs_server_submit": ([_vp, _vp, _vp], _i32),
+    "bs_server_poll": ([_vp, _u64, _vp], _i32),
+    "bs_server_wait": ([_vp, _u64, _i32, _vp], _i32),
+    "bs_server_release": ([_vp, _u64], _i32),
+    "bs_server_copy_result": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
+    "bs_server_get_stats": ([_vp, _vp], _i32),
+    "bs_server_destroy": ([_vp], None),
     "bs_strerror": ([_i32], ctypes.c_char_p),
     "bs_last_device_error": ([], _i32),
     "bs_version": ([], ctypes.c_char_p),
@@ -442,6 +471,86 @@ def bs_batch_launch(batch: Batch, stream=None):
 
 def bs_batch_free(batch: Batch):
     batch.free()
+
+
+# ----------------------------------------------------------------- serving
+def bs_estimate_rows(col: Column, op: str, lit: int, lit2: int = 0) -> int:
+    out = _u64()
+    _check(lib().bs_estimate_rows(col.handle, OPS[op], int(lit), int(lit2), ctypes.byref(out)), "bs_estimate_rows")
+    return out.value
+
+
+class Server:
+    """bs_server: continuous batching over resident columns."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        self._cols = []
+
+    def submit(self, preds, proj=None) -> int:
+        q = bs_query()
+        q.npreds = len(preds)
+        for j, p in enumerate(preds):
+            q.preds[j].col = p[0].handle
+            q.preds[j].op = OPS[p[1]]
+            q.preds[j].lit = int(p[2])
+            q.preds[j].lit2 = int(p[3]) if len(p) > 3 else 0
+        q.proj = proj.handle if proj is not None else None
+        t = _u64()
+        _check(lib().bs_server_submit(self.handle, ctypes.byref(q), ctypes.byref(t)), "bs_server_submit")
+        return t.value
+
+    def _res(self, r: bs_query_result) -> dict:
+        return {"status": r.status, "count": r.count, "d_values": r.d_values, "queue_us": r.queue_us,
+                "latency_us": r.latency_us}
+
+    def poll(self, ticket: int):
+        r = bs_query_result()
+        rc = lib().bs_server_poll(self.handle, ticket, ctypes.byref(r))
+        if rc == BS_ERR_NOT_READY:
+            return None
+        _check(rc, "bs_server_poll")
+        return self._res(r)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> dict:
+        r = bs_query_result()
+        _check(lib().bs_server_wait(self.handle, ticket, int(timeout_ms), ctypes.byref(r)), "bs_server_wait")
+        return self._res(r)
+
+    def values(self, ticket: int, count: int, stream=None):
+        """Copy a finished query's values into a new CUDA int32 tensor."""
+        import torch
+        out = torch.empty(max(1, int(count)), dtype=torch.int32, device="cuda")
+        got = _u64()
+        _check(lib().bs_server_copy_result(self.handle, ticket, _dptr(out), int(count), ctypes.byref(got),
+                                           _stream(stream)), "bs_server_copy_result")
+        return out[: got.value]
+
+    def release(self, ticket: int):
+        _check(lib().bs_server_release(self.handle, ticket), "bs_server_release")
+
+    def stats(self) -> dict:
+        st = bs_server_stats()
+        _check(lib().bs_server_get_stats(self.handle, ctypes.byref(st)), "bs_server_get_stats")
+        return {name: getattr(st, name) for name, _ in st._fields_}
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.bs_server_destroy(h)
+
+    def destroy(self):
+        self.__del__()
+
+
+def bs_server_create(max_batch: int = 0, slots: int = 0, result_bytes: int = 0, scratch_bytes: int = 0,
+                     threads: int = 0, device: int = -1) -> Server:
+    o = bs_server_opts()
+    o.max_batch, o.slots, o.result_bytes, o.scratch_bytes = max_batch, slots, result_bytes, scratch_bytes
+    o.threads, o.device = threads, device
+    h = _vp()
+    _check(lib().bs_server_create(ctypes.byref(o), ctypes.byref(h)), "bs_server_create")
+    return Server(h.value)
 
 
 # ----------------------------------------------------------------- advisor

@@ -1,6 +1,6 @@
 // Batched form: many scan + lookup requests in one persistent, cooperative,
-// CUDA-graph-captured launch (the paper has no counterpart; it serves the
-// batched and serving workloads).
+// CUDA-graph-captured launch, and the serving loop built on it (the paper has
+// no counterpart for either).
 //
 // One kernel, three phases separated by grid-wide barriers (cooperative
 // launch, so every CTA is resident; the barrier is an arrival counter polled
@@ -24,11 +24,17 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <mutex>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "lookup_dev.cuh"
@@ -266,6 +272,66 @@ __global__ void batch_kernel(const BatchK b) {
     }
 }
 
+// ------------------------------------------------------------ request plan
+// Validates request q and fills R's predicate and lookup fields (everything
+// but the scratch pointers). device: -1 on entry for the first request.
+int plan_request(const bs_request &q, BReq &R, int &device, int n_layout[3]) {
+    if (q.npreds < 1 || q.npreds > kMaxPreds || !q.preds[0].col) return BS_ERR_INVALID_ARG;
+    const bs_column *proj = q.proj ? q.proj : q.preds[0].col;
+    const Column &pc = proj->c;
+    if (pc.raw || !pc.d_arena) return BS_ERR_UNSUPPORTED;
+    if (q.out_cap && !q.d_out) return BS_ERR_INVALID_ARG;
+    if (device < 0) device = pc.device;
+    if (pc.device != device) return BS_ERR_INVALID_ARG;
+    R = BReq{};
+    R.npred = q.npreds;
+    for (int p = 0; p < q.npreds; p++) {
+        const bs_column *col = q.preds[p].col;
+        if (!col || col->c.n != pc.n || col->c.device != device) return BS_ERR_INVALID_ARG;
+        if (col->c.raw || !col->c.d_arena) return BS_ERR_UNSUPPORTED;
+        if (q.preds[p].op < BS_LT || q.preds[p].op > BS_BETWEEN) return BS_ERR_INVALID_ARG;
+        KPred kp;
+        const int rc = rewrite_literal(col->c, q.preds[p].op, q.preds[p].lit, q.preds[p].lit2, kp);
+        if (rc) return rc;
+        plan_scan(col->c, kp, nullptr, false, R.pred[p].a, R.pred[p].plan);
+        R.pred[p].a.out = nullptr;  // the batch kernel stores the final word itself
+        if (n_layout) n_layout[col->c.layout]++;
+    }
+    R.look = make_look_args(pc);
+    R.kmax = kmax_for(R.look);
+    R.val1 = pc.d_val1;
+    R.look.out_vals = q.d_out;
+    R.look.out_cap = q.d_out ? q.out_cap : 0;
+    R.look.count = q.d_count;
+    R.n_chunks = R.look.n_chunks;
+    return BS_OK;
+}
+
+// Scratch of one request inside a batch: bit vector (unless supplied),
+// per-chunk counts and offsets.
+size_t request_scratch(const BReq &R, bool own_bits) {
+    const uint64_t nw = (R.look.n + 31) / 32;
+    const size_t a = own_bits ? ((std::max<uint64_t>(4, nw * 4) + 255) & ~(size_t)255) : 0;
+    return a + ((std::max<uint64_t>(4, (uint64_t)R.n_chunks * 4) + 255) & ~(size_t)255) +
+           ((std::max<uint64_t>(8, (uint64_t)R.n_chunks * 8) + 255) & ~(size_t)255);
+}
+
+void bind_scratch(BReq &R, uint8_t *p, uint32_t *user_bits, uint32_t *status) {
+    const uint64_t nw = (R.look.n + 31) / 32;
+    if (user_bits) {
+        R.bits = user_bits;
+    } else {
+        R.bits = (uint32_t *)p;
+        p += (std::max<uint64_t>(4, nw * 4) + 255) & ~(size_t)255;
+    }
+    R.chunk_cnt = (uint32_t *)p;
+    p += (std::max<uint64_t>(4, (uint64_t)R.n_chunks * 4) + 255) & ~(size_t)255;
+    R.chunk_off = (uint64_t *)p;
+    R.look.bits = R.bits;
+    R.look.status = status;
+    for (int q = 0; q < R.npred; q++) R.pred[q].a.status = status;
+}
+
 // ------------------------------------------------------------- tuning cache
 std::mutex g_tune_mu;
 
@@ -410,52 +476,22 @@ int bs_batch_create(const bs_request *reqs, int32_t nreq, const bs_batch_opts *o
     std::vector<uint32_t> unit0(nreq + 1, 0);
     int device = -1;
     size_t scratch = 0;
-    std::vector<size_t> bits_off(nreq, 0), cnt_off(nreq, 0), choff_off(nreq, 0);
+    std::vector<size_t> bits_off(nreq, 0);
     auto take = [&](size_t bytes) {
         size_t at = (scratch + 255) & ~(size_t)255;
         scratch = at + bytes;
         return at;
     };
-    std::string mix;
     uint64_t total_rows = 0;
     int n_layout[3] = {0, 0, 0};
     for (int r = 0; r < nreq; r++) {
         const bs_request &q = reqs[r];
-        if (q.npreds < 1 || q.npreds > kMaxPreds || !q.preds[0].col) return BS_ERR_INVALID_ARG;
-        const bs_column *proj = q.proj ? q.proj : q.preds[0].col;
-        const Column &pc = proj->c;
-        if (pc.raw || !pc.d_arena) return BS_ERR_UNSUPPORTED;
-        if (q.out_cap && !q.d_out) return BS_ERR_INVALID_ARG;
-        if (device < 0) device = pc.device;
-        if (pc.device != device) return BS_ERR_INVALID_ARG;
+        const int prc = plan_request(q, h[r], device, n_layout);
+        if (prc) return prc;
         BReq &R = h[r];
-        R = BReq{};
-        R.npred = q.npreds;
-        for (int p = 0; p < q.npreds; p++) {
-            const bs_column *col = q.preds[p].col;
-            if (!col || col->c.n != pc.n || col->c.device != device) return BS_ERR_INVALID_ARG;
-            if (col->c.raw || !col->c.d_arena) return BS_ERR_UNSUPPORTED;
-            if (q.preds[p].op < BS_LT || q.preds[p].op > BS_BETWEEN) return BS_ERR_INVALID_ARG;
-            KPred kp;
-            int rc = rewrite_literal(col->c, q.preds[p].op, q.preds[p].lit, q.preds[p].lit2, kp);
-            if (rc) return rc;
-            plan_scan(col->c, kp, nullptr, false, R.pred[p].a, R.pred[p].plan);
-            R.pred[p].a.out = nullptr;  // the batch kernel stores the final word itself
-            n_layout[col->c.layout]++;
-        }
-        R.look = make_look_args(pc);
-        R.kmax = kmax_for(R.look);
-        R.val1 = pc.d_val1;
-        R.look.out_vals = q.d_out;
-        R.look.out_cap = q.d_out ? q.out_cap : 0;
-        R.look.count = q.d_count;
-        R.n_chunks = R.look.n_chunks;
         unit0[r] = (r ? unit0[r - 1] + h[r - 1].n_chunks : 0);
-        total_rows += pc.n;
-        const uint64_t nw = (pc.n + 31) / 32;
-        bits_off[r] = q.d_bits ? SIZE_MAX : take(std::max<uint64_t>(4, nw * 4));
-        cnt_off[r] = take(std::max<uint64_t>(4, (uint64_t)R.n_chunks * 4));
-        choff_off[r] = take(std::max<uint64_t>(8, (uint64_t)R.n_chunks * 8));
+        total_rows += R.look.n;
+        bits_off[r] = take(request_scratch(R, q.d_bits == nullptr));
     }
     unit0[nreq] = unit0[nreq - 1] + h[nreq - 1].n_chunks;
     const size_t o_ctr = take(256);
@@ -479,14 +515,8 @@ int bs_batch_create(const bs_request *reqs, int32_t nreq, const bs_batch_opts *o
         uint32_t *status = status_word();
         if (!status) rc = BS_ERR_CUDA;
         for (int r = 0; r < nreq && rc == BS_OK; r++) {
-            BReq &R = h[r];
-            R.bits = reqs[r].d_bits ? reqs[r].d_bits : (uint32_t *)(base + bits_off[r]);
-            R.chunk_cnt = (uint32_t *)(base + cnt_off[r]);
-            R.chunk_off = (uint64_t *)(base + choff_off[r]);
-            R.unit0 = unit0[r];
-            R.look.bits = R.bits;
-            R.look.status = status;
-            for (int p = 0; p < R.npred; p++) R.pred[p].a.status = status;
+            bind_scratch(h[r], base + bits_off[r], reqs[r].d_bits, status);
+            h[r].unit0 = unit0[r];
         }
         b->k.reqs = (const BReq *)(base + o_reqs);
         b->k.unit0 = (const uint32_t *)(base + o_unit0);
@@ -581,6 +611,480 @@ void bs_batch_free(bs_batch *b) {
     if (b->d_arena) cudaFree(b->d_arena);
     cudaSetDevice(prev);
     delete b;
+}
+
+}  // extern "C"
+
+// ================================================================== server
+// Dispatcher thread: completions first (events of the batches in flight),
+// then admission in arrival order into every free slot, then a short spin.
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double us_since(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::micro>(b - a).count();
+}
+
+// First-fit allocator over an offset range [0, cap) (256-byte granules).
+class RangeAlloc {
+  public:
+    explicit RangeAlloc(size_t cap = 0) { reset(cap); }
+    void reset(size_t cap) {
+        free_.clear();
+        if (cap) free_[0] = cap;
+        used_ = 0;
+    }
+    bool alloc(size_t bytes, size_t &off) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                off = it->first;
+                const size_t rest = it->second - bytes;
+                free_.erase(it);
+                if (rest) free_[off + bytes] = rest;
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+
+  private:
+    std::map<size_t, size_t> free_;
+    size_t used_ = 0;
+};
+
+struct QueryRec {
+    bs::BReq plan;
+    uint64_t bound = 0;           // upper bound of selected rows
+    size_t out_bytes = 0, out_off = SIZE_MAX;
+    size_t scratch_bytes = 0, scratch_off = SIZE_MAX;
+    int state = 0;                // 0 queued, 1 running, 2 done
+    uint64_t count = 0;
+    Clock::time_point t_submit, t_launch, t_done;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    uint8_t *d_desc = nullptr;    // BReq[max_batch] | unit0 | ctr | counts
+    uint8_t *h_desc = nullptr;    // pinned mirror
+    size_t desc_bytes = 0, o_unit0 = 0, o_ctr = 0, o_counts = 0;
+    bool busy = false;
+    std::vector<uint64_t> tickets;
+};
+
+}  // namespace
+
+struct bs_server {
+    bs_server_opts o{};
+    int device = 0;
+    uint8_t *d_result = nullptr, *d_scratch = nullptr;
+    RangeAlloc result_alloc, scratch_alloc;
+    std::vector<Slot> slots;
+    int threads = 256, ctas = 1;
+    uint32_t *status = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> queue;
+    std::unordered_map<uint64_t, QueryRec> recs;
+    uint64_t next_ticket = 1;
+    bs_server_stats stats{};
+    uint64_t batched_queries = 0;
+    bool stop = false;
+    std::thread th;
+};
+
+namespace {
+
+// Launches the batch of `slot` (descriptors already in its pinned mirror).
+int launch_slot(bs_server *S, Slot &sl, int nreq, uint32_t total_units) {
+    using namespace bs;
+    BatchK k{};
+    k.reqs = (const BReq *)sl.d_desc;
+    k.unit0 = (const uint32_t *)(sl.d_desc + sl.o_unit0);
+    k.nreq = nreq;
+    k.total_units = total_units;
+    k.ctr = (uint32_t *)(sl.d_desc + sl.o_ctr);
+    k.status = S->status;
+    if (cudaMemcpyAsync(sl.d_desc, sl.h_desc, sl.o_ctr, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+        return BS_ERR_CUDA;
+    if (cudaMemsetAsync(k.ctr, 0, 4 * sizeof(uint32_t), sl.stream) != cudaSuccess) return BS_ERR_CUDA;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)S->ctas);
+    cfg.blockDim = dim3((unsigned)S->threads);
+    cfg.dynamicSmemBytes = smem_bytes(S->threads);
+    cfg.stream = sl.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, batch_kernel, k) != cudaSuccess) return BS_ERR_CUDA;
+    if (cudaMemcpyAsync(sl.h_desc + sl.o_counts, sl.d_desc + sl.o_counts, (size_t)nreq * 8, cudaMemcpyDeviceToHost,
+                        sl.stream) != cudaSuccess)
+        return BS_ERR_CUDA;
+    if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return BS_ERR_CUDA;
+    return BS_OK;
+}
+
+void dispatcher(bs_server *S) {
+    using namespace bs;
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (true) {
+        bool progress = false;
+        // completions
+        for (Slot &sl : S->slots) {
+            if (!sl.busy || cudaEventQuery(sl.done) != cudaSuccess) continue;
+            const auto now = Clock::now();
+            const uint64_t *counts = (const uint64_t *)(sl.h_desc + sl.o_counts);
+            for (size_t i = 0; i < sl.tickets.size(); i++) {
+                QueryRec &q = S->recs[sl.tickets[i]];
+                q.count = counts[i];
+                q.t_done = now;
+                q.state = 2;
+                S->scratch_alloc.release(q.scratch_off, q.scratch_bytes);
+                q.scratch_off = SIZE_MAX;
+                S->stats.completed++;
+            }
+            sl.tickets.clear();
+            sl.busy = false;
+            progress = true;
+            S->cv_done.notify_all();
+        }
+        // admission and launch
+        for (Slot &sl : S->slots) {
+            if (sl.busy || S->queue.empty()) continue;
+            const int maxb = S->o.max_batch;
+            BReq *reqs = (BReq *)sl.h_desc;
+            uint32_t *unit0 = (uint32_t *)(sl.h_desc + sl.o_unit0);
+            uint64_t *d_counts = (uint64_t *)(sl.d_desc + sl.o_counts);
+            int nb = 0;
+            uint32_t units = 0;
+            while (nb < maxb && !S->queue.empty()) {
+                const uint64_t tk = S->queue.front();
+                QueryRec &q = S->recs[tk];
+                size_t ro = SIZE_MAX, so = SIZE_MAX;
+                if (!S->result_alloc.alloc(q.out_bytes, ro)) break;        // wait for releases
+                if (!S->scratch_alloc.alloc(q.scratch_bytes, so)) {         // wait for completions
+                    S->result_alloc.release(ro, q.out_bytes);
+                    break;
+                }
+                q.out_off = ro;
+                q.scratch_off = so;
+                BReq R = q.plan;
+                R.look.out_vals = (int32_t *)(S->d_result + ro);
+                R.look.out_cap = q.bound;
+                R.look.count = d_counts + nb;
+                bind_scratch(R, S->d_scratch + so, nullptr, S->status);
+                R.unit0 = units;
+                unit0[nb] = units;
+                units += R.n_chunks;
+                reqs[nb] = R;
+                sl.tickets.push_back(tk);
+                q.state = 1;
+                S->queue.pop_front();
+                nb++;
+            }
+            if (nb == 0) break;  // memory is full: wait for completions or releases
+            unit0[nb] = units;
+            const auto now = Clock::now();
+            for (uint64_t tk : sl.tickets) S->recs[tk].t_launch = now;
+            if (launch_slot(S, sl, nb, units) != BS_OK) {
+                // record the failure on the queries; they complete with count 0
+                for (uint64_t tk : sl.tickets) {
+                    QueryRec &q = S->recs[tk];
+                    q.state = 2;
+                    q.t_done = Clock::now();
+                    S->scratch_alloc.release(q.scratch_off, q.scratch_bytes);
+                    q.scratch_off = SIZE_MAX;
+                }
+                sl.tickets.clear();
+                S->cv_done.notify_all();
+                continue;
+            }
+            sl.busy = true;
+            S->stats.batches++;
+            S->batched_queries += (uint64_t)nb;
+            progress = true;
+        }
+        bool any_busy = false;
+        for (Slot &sl : S->slots) any_busy |= sl.busy;
+        if (S->stop && !any_busy) break;
+        if (!progress) {
+            if (any_busy) {
+                // batches in flight: poll their events (a timed sleep would
+                // oversleep by tens of microseconds)
+                lk.unlock();
+                std::this_thread::yield();
+                lk.lock();
+            } else {
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+            }
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int bs_estimate_rows(const bs_column *col, bs_op op, int32_t lit, int32_t lit2, uint64_t *out) {
+    if (!col || !out || op < BS_LT || op > BS_BETWEEN) return BS_ERR_INVALID_ARG;
+    *out = bs::estimate_rows(col->c, op, lit, lit2);
+    return BS_OK;
+}
+
+int bs_server_create(const bs_server_opts *opts, bs_server **out) {
+    using namespace bs;
+    if (!out) return BS_ERR_INVALID_ARG;
+    *out = nullptr;
+    auto *S = new (std::nothrow) bs_server;
+    if (!S) return BS_ERR_OOM;
+    bs_server_opts o{};
+    o.device = -1;
+    if (opts) o = *opts;
+    if (o.max_batch <= 0) o.max_batch = 64;
+    if (o.slots <= 0) o.slots = 2;
+    if (o.result_bytes == 0) o.result_bytes = 1ull << 30;
+    if (o.scratch_bytes == 0) o.scratch_bytes = 4ull << 30;
+    if (o.threads <= 0) o.threads = 256;
+    if (o.max_batch > 4096 || o.slots > 16) {
+        delete S;
+        return BS_ERR_INVALID_ARG;
+    }
+    S->o = o;
+    int dev = o.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
+        delete S;
+        return BS_ERR_CUDA;
+    }
+    S->device = dev;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    int rc = cudaSetDevice(dev) == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+    if (rc == BS_OK) {
+        S->status = status_word();
+        if (!S->status) rc = BS_ERR_CUDA;
+    }
+    if (rc == BS_OK && (cudaMalloc(&S->d_result, o.result_bytes) != cudaSuccess ||
+                        cudaMalloc(&S->d_scratch, o.scratch_bytes) != cudaSuccess)) {
+        cudaGetLastError();
+        rc = BS_ERR_OOM;
+    }
+    S->result_alloc.reset(o.result_bytes);
+    S->scratch_alloc.reset(o.scratch_bytes);
+    if (rc == BS_OK) {
+        // kernel shape: each slot's grid takes its share of the GPU, so batches
+        // of different slots run side by side
+        const size_t smem = smem_bytes(o.threads);
+        int fit = 0;
+        if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel, o.threads, smem) != cudaSuccess ||
+            fit < 1) {
+            cudaGetLastError();
+            rc = BS_ERR_CUDA;
+        }
+        S->threads = o.threads;
+        S->ctas = std::max(1, fit * sm_count(dev) / o.slots);
+    }
+    S->slots.resize(o.slots);
+    for (Slot &sl : S->slots) {
+        if (rc != BS_OK) break;
+        size_t at = 0;
+        auto take = [&](size_t bytes) {
+            size_t a = (at + 255) & ~(size_t)255;
+            at = a + bytes;
+            return a;
+        };
+        take(sizeof(BReq) * (size_t)o.max_batch);
+        sl.o_unit0 = take(((size_t)o.max_batch + 1) * 4);
+        sl.o_ctr = take(256);
+        sl.o_counts = take((size_t)o.max_batch * 8);
+        sl.desc_bytes = at;
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&sl.d_desc, sl.desc_bytes) != cudaSuccess ||
+            cudaMallocHost(&sl.h_desc, sl.desc_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            rc = BS_ERR_OOM;
+        }
+    }
+    cudaSetDevice(prev);
+    if (rc != BS_OK) {
+        bs_server_destroy(S);
+        return rc;
+    }
+    S->th = std::thread(dispatcher, S);
+    *out = S;
+    return BS_OK;
+}
+
+int bs_server_submit(bs_server *S, const bs_query *q, uint64_t *ticket) {
+    using namespace bs;
+    if (!S || !q || !ticket) return BS_ERR_INVALID_ARG;
+    QueryRec rec;
+    bs_request r{};
+    r.npreds = q->npreds;
+    for (int i = 0; i < BS_MAX_CONJ; i++) r.preds[i] = q->preds[i];
+    r.proj = q->proj;
+    int device = S->device;
+    int rc = plan_request(r, rec.plan, device, nullptr);
+    if (rc) return rc;
+    if (device != S->device) return BS_ERR_INVALID_ARG;
+    uint64_t bound = rec.plan.look.n;
+    for (int i = 0; i < q->npreds; i++)
+        bound = std::min(bound, estimate_rows(q->preds[i].col->c, q->preds[i].op, q->preds[i].lit, q->preds[i].lit2));
+    rec.bound = bound;
+    rec.out_bytes = std::max<uint64_t>(256, bound * 4);
+    rec.scratch_bytes = request_scratch(rec.plan, true);
+    if (rec.out_bytes > S->o.result_bytes || rec.scratch_bytes > S->o.scratch_bytes) {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stats.rejected++;
+        return BS_ERR_CAPACITY;
+    }
+    rec.t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        const uint64_t tk = S->next_ticket++;
+        S->recs.emplace(tk, rec);
+        S->queue.push_back(tk);
+        S->stats.submitted++;
+        *ticket = tk;
+    }
+    S->cv_work.notify_one();
+    return BS_OK;
+}
+
+static int fill_result(bs_server *S, const QueryRec &q, bs_query_result *res) {
+    std::memset(res, 0, sizeof *res);
+    if (q.state != 2) {
+        res->status = BS_ERR_NOT_READY;
+        return BS_ERR_NOT_READY;
+    }
+    res->status = BS_OK;
+    res->count = q.count;
+    res->d_values = q.out_off == SIZE_MAX ? nullptr : (const int32_t *)(S->d_result + q.out_off);
+    res->queue_us = us_since(q.t_submit, q.t_launch);
+    res->latency_us = us_since(q.t_submit, q.t_done);
+    return BS_OK;
+}
+
+int bs_server_poll(bs_server *S, uint64_t ticket, bs_query_result *res) {
+    if (!S || !res) return BS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->recs.find(ticket);
+    if (it == S->recs.end()) return BS_ERR_INVALID_ARG;
+    return fill_result(S, it->second, res);
+}
+
+int bs_server_wait(bs_server *S, uint64_t ticket, int32_t timeout_ms, bs_query_result *res) {
+    if (!S || !res) return BS_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->recs.find(ticket);
+    if (it == S->recs.end()) return BS_ERR_INVALID_ARG;
+    const bool ok = S->cv_done.wait_for(lk, std::chrono::milliseconds(std::max(0, timeout_ms)),
+                                        [&] { return S->recs[ticket].state == 2; });
+    if (!ok) {
+        std::memset(res, 0, sizeof *res);
+        res->status = BS_ERR_NOT_READY;
+        return BS_ERR_TIMEOUT;
+    }
+    return fill_result(S, S->recs[ticket], res);
+}
+
+int bs_server_copy_result(bs_server *S, uint64_t ticket, int32_t *dst, uint64_t cap, uint64_t *copied,
+                          void *stream) {
+    if (!S || (cap && !dst)) return BS_ERR_INVALID_ARG;
+    const int32_t *src = nullptr;
+    uint64_t n = 0;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        auto it = S->recs.find(ticket);
+        if (it == S->recs.end()) return BS_ERR_INVALID_ARG;
+        if (it->second.state != 2) return BS_ERR_NOT_READY;
+        if (it->second.out_off == SIZE_MAX) return BS_ERR_INVALID_ARG;
+        src = (const int32_t *)(S->d_result + it->second.out_off);
+        n = std::min(cap, it->second.count);
+    }
+    if (copied) *copied = n;
+    if (n && cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDefault, (cudaStream_t)stream) != cudaSuccess)
+        return BS_ERR_CUDA;
+    return BS_OK;
+}
+
+int bs_server_release(bs_server *S, uint64_t ticket) {
+    if (!S) return BS_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        auto it = S->recs.find(ticket);
+        if (it == S->recs.end()) return BS_ERR_INVALID_ARG;
+        if (it->second.state != 2) return BS_ERR_NOT_READY;
+        if (it->second.out_off != SIZE_MAX) S->result_alloc.release(it->second.out_off, it->second.out_bytes);
+        S->recs.erase(it);
+    }
+    S->cv_work.notify_one();
+    return BS_OK;
+}
+
+int bs_server_get_stats(const bs_server *S, bs_server_stats *st) {
+    if (!S || !st) return BS_ERR_INVALID_ARG;
+    auto *M = const_cast<bs_server *>(S);
+    std::lock_guard<std::mutex> g(M->mu);
+    *st = S->stats;
+    st->mean_batch = S->stats.batches ? (double)S->batched_queries / (double)S->stats.batches : 0.0;
+    st->result_bytes_in_use = S->result_alloc.used();
+    st->scratch_bytes_in_use = S->scratch_alloc.used();
+    st->queued = S->queue.size();
+    return BS_OK;
+}
+
+void bs_server_destroy(bs_server *S) {
+    if (!S) return;
+    if (S->th.joinable()) {
+        {
+            std::lock_guard<std::mutex> g(S->mu);
+            S->stop = true;
+            S->queue.clear();  // queued queries are dropped; running batches finish
+        }
+        S->cv_work.notify_all();
+        S->th.join();
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(S->device);
+    for (Slot &sl : S->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.d_desc) cudaFree(sl.d_desc);
+        if (sl.h_desc) cudaFreeHost(sl.h_desc);
+    }
+    if (S->d_result) cudaFree(S->d_result);
+    if (S->d_scratch) cudaFree(S->d_scratch);
+    cudaSetDevice(prev);
+    delete S;
 }
 
 }  // extern "C"

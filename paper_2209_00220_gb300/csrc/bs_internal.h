@@ -75,6 +75,7 @@ struct Column {
     std::vector<uint64_t> dcode;  // PP-VBS: code of dict[i] (unpadded)
     std::vector<uint8_t> dlen;    // PP-VBS: its length in bytes
     std::vector<uint64_t> dcount; // rows holding dict[i] (observed dictionaries)
+    std::vector<uint64_t> dcum;   // prefix sums of dcount (dict.size() + 1 entries)
     std::vector<uint64_t> first_byte_rows;  // PP-VBS: rows whose code starts with byte b
     std::vector<int32_t> val2;    // PP-VBS decode: value of codes <= 2 bytes, by first two bytes
     std::vector<uint32_t> leaf2;  // PP-VBS decode: first dictionary index of a level-2 leaf
@@ -114,6 +115,7 @@ int encode_raw(const uint64_t *codes, const uint8_t *lens, uint64_t n, bs_layout
 int rewrite_literal(const Column &c, int op, int32_t lit, int32_t lit2, KPred &out);
 int make_code_pred(const Column &c, int op, uint64_t code, int len, uint64_t code2, int len2, KPred &out);
 int resolve_threads(int requested);
+uint64_t estimate_rows(const Column &c, int op, int32_t lit, int32_t lit2);
 
 // effective-bytes counter (bytes_model.cpp); tile_stride > 1 samples every
 // tile_stride-th tile and scales up

@@ -438,6 +438,8 @@ int encode_values(const int32_t *values, uint64_t n, bs_layout layout, const bs_
             if (rc) return rc;
             ppe_numerical(Q, c.dcode, c.dlen, T);
             c.dcount = Q;
+            c.dcum.assign(Q.size() + 1, 0);
+            for (size_t i = 0; i < Q.size(); i++) c.dcum[i + 1] = c.dcum[i] + Q[i];
             build_decode_tables(c);
             c.first_byte_rows.assign(256, 0);
             for (size_t i = 0; i < Q.size(); i++)
@@ -491,6 +493,9 @@ int encode_values(const int32_t *values, uint64_t n, bs_layout layout, const bs_
                 std::vector<uint64_t> Q;
                 int rc = build_dictionary(values, n, T, c.dict, Q, ridx);
                 if (rc) return rc;
+                c.dcount = Q;
+                c.dcum.assign(Q.size() + 1, 0);
+                for (size_t i = 0; i < Q.size(); i++) c.dcum[i + 1] = c.dcum[i] + Q[i];
             }
             c.k = code_bits_for(c.dict.size());
             ri = ridx.data();
@@ -659,6 +664,32 @@ int make_code_pred(const Column &c, int op, uint64_t code, int len, uint64_t cod
         if (rc) return rc;
     }
     return BS_OK;
+}
+
+}  // namespace bs
+
+namespace bs {
+
+// Rows whose value satisfies (op, lit, lit2), from the dictionary counts when
+// the column has them (else every row).
+uint64_t estimate_rows(const Column &c, int op, int32_t lit, int32_t lit2) {
+    if (c.dcum.size() != c.dict.size() + 1 || c.dict.empty()) return c.n;
+    auto below = [&](int64_t x) -> uint64_t {  // rows with value < x
+        if (x > INT32_MAX) return c.n;
+        if (x <= INT32_MIN) return 0;
+        const size_t u = (size_t)(std::lower_bound(c.dict.begin(), c.dict.end(), (int32_t)x) - c.dict.begin());
+        return c.dcum[u];
+    };
+    const int64_t x = lit, y = lit2;
+    switch (op) {
+    case BS_LT: return below(x);
+    case BS_LE: return below(x + 1);
+    case BS_GT: return c.n - below(x + 1);
+    case BS_GE: return c.n - below(x);
+    case BS_EQ: return below(x + 1) - below(x);
+    case BS_NE: return c.n - (below(x + 1) - below(x));
+    default: return x > y ? 0 : below(y + 1) - below(x);
+    }
 }
 
 }  // namespace bs
