@@ -61,8 +61,16 @@ typedef struct bs_column bs_column; /* opaque; owns its device buffers */
  *       (1 <= domain_bits <= 32). 0 = use a dictionary instead.
  *   domain_values / n_domain: for BS_BYTESLICE and BS_BITPACKED, a declared
  *       dictionary (distinct int32 values in any order); code = rank of the
- *       value in it. NULL = the column's observed distinct values. PP-VBS always
- *       encodes the observed values with their frequencies (Algorithm 1).
+ *       value in it. NULL = the column's observed distinct values. PP-VBS
+ *       encodes the observed values with their frequencies (Algorithm 1)
+ *       unless domain_counts is also given.
+ *   domain_counts: with domain_values, for BS_PPVBS: the frequency of each
+ *       declared value (same order, n_domain entries) that Algorithm 1 builds
+ *       the codes from, instead of the column's own counts. A row shard of a
+ *       larger column passes the whole column's dictionary and counts, so
+ *       every shard gets the same codes and the shards' results concatenate
+ *       to the whole column's. Every value of the column must be declared
+ *       (else INVALID_ARG); declared values must be distinct.
  *   device: CUDA device ordinal, -1 = the current device.
  *   host_only: 1 = build the layout in host memory only (no GPU needed); such a
  *       column answers bs_column_row_codes / bs_column_get_info but not scans.
@@ -78,6 +86,7 @@ typedef struct {
     int32_t keep_host;
     int32_t threads;
     int32_t reserved;
+    const uint64_t *domain_counts;
 } bs_encode_opts;
 
 /* ------------------------------------------------------------- columns */

@@ -30,7 +30,7 @@ _u64, _i32, _i64, _vp = ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, ctypes.
 class bs_encode_opts(ctypes.Structure):
     _fields_ = [("domain_bits", _i32), ("device", _i32), ("domain_min", _i64), ("domain_values", _vp),
                 ("n_domain", _u64), ("host_only", _i32), ("keep_host", _i32), ("threads", _i32),
-                ("reserved", _i32)]
+                ("reserved", _i32), ("domain_counts", _vp)]
 
 
 class bs_column_info(ctypes.Structure):
@@ -183,7 +183,7 @@ def _np(a, dtype):
 
 
 def _opts(domain_bits=0, domain_min=0, domain_values=None, device=-1, host_only=False, keep_host=False,
-          threads=0):
+          threads=0, domain_counts=None):
     o = bs_encode_opts()
     o.domain_bits = int(domain_bits)
     o.domain_min = int(domain_min)
@@ -191,11 +191,20 @@ def _opts(domain_bits=0, domain_min=0, domain_values=None, device=-1, host_only=
     o.host_only = 1 if host_only else 0
     o.keep_host = 1 if keep_host else 0
     o.threads = int(threads)
-    keep = None
+    keep = []
     if domain_values is not None:
-        keep = _np(domain_values, np.int32)
-        o.domain_values = keep.ctypes.data
-        o.n_domain = keep.size
+        dv = _np(domain_values, np.int32)
+        keep.append(dv)
+        o.domain_values = dv.ctypes.data
+        o.n_domain = dv.size
+        if domain_counts is not None:
+            dc = _np(domain_counts, np.uint64)
+            if dc.size != dv.size:
+                raise ValueError("domain_counts needs one count per domain value")
+            keep.append(dc)
+            o.domain_counts = dc.ctypes.data
+    elif domain_counts is not None:
+        raise ValueError("domain_counts needs domain_values")
     return o, keep
 
 
@@ -487,7 +496,9 @@ class Server:
         self.handle = handle
         self._cols = []
 
-    def submit(self, preds, proj=None) -> int:
+    @staticmethod
+    def prepare(preds, proj=None) -> bs_query:
+        """The bs_query for (preds, proj), built ahead of submission."""
         q = bs_query()
         q.npreds = len(preds)
         for j, p in enumerate(preds):
@@ -496,6 +507,11 @@ class Server:
             q.preds[j].lit = int(p[2])
             q.preds[j].lit2 = int(p[3]) if len(p) > 3 else 0
         q.proj = proj.handle if proj is not None else None
+        return q
+
+    def submit(self, preds, proj=None) -> int:
+        """preds: [(Column, op, lit[, lit2]), ...], or a bs_query from prepare()."""
+        q = preds if isinstance(preds, bs_query) else self.prepare(preds, proj)
         t = _u64()
         _check(lib().bs_server_submit(self.handle, ctypes.byref(q), ctypes.byref(t)), "bs_server_submit")
         return t.value

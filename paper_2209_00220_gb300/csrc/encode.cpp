@@ -415,6 +415,52 @@ static void emit_bitpacked(Column &c, Get get, int T) {
     c.len_hist[(k + 7) / 8] = c.n;
 }
 
+// Declared dictionary with counts: A sorted, Q permuted alongside, and every
+// row's index in A (INVALID_ARG for an undeclared value or a repeated one).
+static int declared_dictionary(const int32_t *v, uint64_t n, int T, const bs_encode_opts &o,
+                               std::vector<int32_t> &A, std::vector<uint64_t> &Q, std::vector<uint32_t> &ridx) {
+    if (!o.domain_values || o.n_domain == 0 || o.n_domain > (1ull << 32)) return BS_ERR_INVALID_ARG;
+    std::vector<uint32_t> order(o.n_domain);
+    for (uint64_t i = 0; i < o.n_domain; i++) order[i] = (uint32_t)i;
+    std::sort(order.begin(), order.end(),
+              [&](uint32_t a, uint32_t b) { return o.domain_values[a] < o.domain_values[b]; });
+    A.resize(o.n_domain);
+    Q.resize(o.n_domain);
+    for (uint64_t i = 0; i < o.n_domain; i++) {
+        A[i] = o.domain_values[order[i]];
+        Q[i] = o.domain_counts[order[i]];
+        if (i && A[i] == A[i - 1]) return BS_ERR_INVALID_ARG;
+    }
+    ridx.assign(n, 0);
+    std::atomic<bool> bad{false};
+    parallel_for(n, T, [&](uint64_t b, uint64_t e, int) {
+        for (uint64_t i = b; i < e; i++) {
+            auto it = std::lower_bound(A.begin(), A.end(), v[i]);
+            if (it == A.end() || *it != v[i]) { bad = true; return; }
+            ridx[i] = (uint32_t)(it - A.begin());
+        }
+    });
+    return bad ? BS_ERR_INVALID_ARG : BS_OK;
+}
+
+// Q[i] = rows of this column whose value is A[i].
+static void count_rows(const std::vector<uint32_t> &ridx, size_t nd, int T, std::vector<uint64_t> &Q) {
+    Q.assign(nd, 0);
+    const uint64_t n = ridx.size();
+    const uint64_t tt = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)T, (n >> 16) + 1));
+    if (tt == 1 || (uint64_t)nd * tt * 8 > (1ull << 30)) {
+        for (uint32_t i : ridx) Q[i]++;
+        return;
+    }
+    std::vector<std::vector<uint64_t>> part(tt);
+    parallel_for(n, (int)tt, [&](uint64_t b, uint64_t e, int t) {
+        part[t].assign(nd, 0);
+        for (uint64_t i = b; i < e; i++) part[t][ridx[i]]++;
+    }, 1);
+    for (auto &h : part)
+        for (size_t i = 0; i < h.size(); i++) Q[i] += h[i];
+}
+
 static int code_bits_for(uint64_t count) {  // max(1, ceil(log2(count)))
     int k = 0;
     while (k < 63 && (1ull << k) < count) k++;
@@ -434,9 +480,18 @@ int encode_values(const int32_t *values, uint64_t n, bs_layout layout, const bs_
         if (layout == BS_PPVBS) {
             std::vector<uint64_t> Q;
             std::vector<uint32_t> ridx;
-            int rc = build_dictionary(values, n, T, c.dict, Q, ridx);
-            if (rc) return rc;
-            ppe_numerical(Q, c.dcode, c.dlen, T);
+            if (o.domain_counts) {
+                // codes from the declared dictionary's counts (a row shard of a
+                // larger column); Q below is then recounted over this column's rows
+                int rc = declared_dictionary(values, n, T, o, c.dict, Q, ridx);
+                if (rc) return rc;
+                ppe_numerical(Q, c.dcode, c.dlen, T);
+                count_rows(ridx, c.dict.size(), T, Q);
+            } else {
+                int rc = build_dictionary(values, n, T, c.dict, Q, ridx);
+                if (rc) return rc;
+                ppe_numerical(Q, c.dcode, c.dlen, T);
+            }
             c.dcount = Q;
             c.dcum.assign(Q.size() + 1, 0);
             for (size_t i = 0; i < Q.size(); i++) c.dcum[i + 1] = c.dcum[i] + Q[i];

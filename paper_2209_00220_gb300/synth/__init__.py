@@ -171,6 +171,61 @@ def config_sweep_column(n: int, d: int, s: float, seed: int, monotone: bool = Fa
     return r.view(np.int32)
 
 
+def _uniform01(seed: int, stream: int, n: int) -> np.ndarray:
+    """n doubles in [0, 1) from the top 53 bits of the counter generator."""
+    return (u64(seed, stream, n) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+def lognormal_amounts(n: int, mu: float, sigma: float, cap_bits: int, seed: int) -> np.ndarray:
+    """Heavy-tailed non-negative amounts: floor(exp(mu + sigma z)) with z standard
+    normal (Box-Muller over two counter streams), capped at 2^cap_bits - 1."""
+    u1 = _uniform01(seed, 31, n)
+    u2 = _uniform01(seed, 32, n)
+    z = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+    a = np.floor(np.exp(mu + sigma * z))
+    return np.minimum(a, float((1 << cap_bits) - 1)).astype(np.int32)
+
+
+# (name, kind, parameters) of the 20 columns of the synthetic denormalised wide
+# table: 5 categorical, 4 date-like day counts, 1 monotone id, 4 heavy-tailed
+# amounts, 6 mixed uniform / Zipf columns.
+WIDE_TABLE = (
+    ("cat_2", "categorical", (2, 0.0)), ("cat_16", "categorical", (16, 0.5)),
+    ("cat_256", "categorical", (256, 1.0)), ("cat_4k", "categorical", (4096, 1.5)),
+    ("cat_64k", "categorical", (65536, 0.8)),
+    ("day_a", "date", (0.0,)), ("day_b", "date", (0.0,)), ("day_c", "date", (0.7,)), ("day_d", "date", (1.2,)),
+    ("id", "monotone", (1000,)),
+    ("amt_a", "amount", (4.0, 1.0, 20)), ("amt_b", "amount", (6.0, 1.5, 24)),
+    ("amt_c", "amount", (8.0, 2.0, 24)), ("amt_d", "amount", (3.0, 0.5, 16)),
+    ("mix_10", "mixed", (10, 0.0)), ("mix_13", "mixed", (13, 1.2)), ("mix_16", "mixed", (16, 0.0)),
+    ("mix_19", "mixed", (19, 0.7)), ("mix_22", "mixed", (22, 0.0)), ("mix_24", "mixed", (24, 1.5)),
+)
+
+
+def wide_table_column(name: str, n: int, seed: int = 0) -> np.ndarray:
+    """One column of the wide table (see WIDE_TABLE), n rows."""
+    i = [w[0] for w in WIDE_TABLE].index(name)
+    _, kind, p = WIDE_TABLE[i]
+    cs = seed * 100 + i
+    if kind == "categorical":
+        card, s = p
+        table = distinct_values(card, cs)[permutation(card, cs)]
+        return zipf_column(n, card, s, cs, mapping=table)
+    if kind == "date":
+        # day counts 0..3650; s > 0: a seeded order of the days is Zipf-weighted
+        (s,) = p
+        days = permutation(3651, cs).astype(np.int32)
+        return zipf_column(n, 3651, s, cs, mapping=days)
+    if kind == "monotone":
+        (off,) = p
+        return (np.arange(n, dtype=np.int64) + off).astype(np.int32)
+    if kind == "amount":
+        mu, sigma, cap = p
+        return lognormal_amounts(n, mu, sigma, cap, cs)
+    d, s = p
+    return config_sweep_column(n, d, s, cs)
+
+
 def domain_min_for_bits(d: int) -> int:
     return -(1 << 31) if d == 32 else 0
 
