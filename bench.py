@@ -13,6 +13,17 @@ Under torchrun (N > 1) every rank holds its own 2^30-row shard (rows are
 independent; no collective is on the data path) and the value is the rows of
 all ranks over the slowest rank's time (weak scaling).
 
+Beside the step, the line carries two more measurements (skip them with
+--no-batched / --no-serving):
+  batched: 256 scan+lookup requests over a pool of 32 resident columns
+    (2^20..2^28 rows, log-uniform; 8..32-bit codes; Zipf s in [0, 1.5]; all
+    three layouts), run as one persistent graph-captured launch vs 256 plain
+    scan+lookup launch pairs, with identical outputs checked;
+  serving: 16 resident PP-VBS columns (4 tables of 4 columns, 2^28..2^30
+    rows), Poisson arrivals at 1k..100k queries/s of 1-3-predicate
+    conjunctions + lookup at 0.01%..10% selectivity, through the serving loop
+    vs serial plain execution: throughput, p50/p99 latency, identical results.
+
 --impl reference times the CPU oracle (plain C: decode every row from the
 layout, evaluate the predicate on the plain value, gather values) on a bounded
 sample of the same column on the host cores.
@@ -41,6 +52,33 @@ def _peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def profile_traffic(name: str):
+    """DRAM bytes per launch of a kernel at the bench's full size, from the
+    committed ncu summary profiles/<name>.md (its 'traffic_bytes_full_launch'
+    line), or None when the summary is missing or the kernel sources it names
+    ('sources' line) no longer hash to its 'sources_sha256' line."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", name + ".md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+    try:
+        h = hashlib.sha256()
+        for src in fields["sources"].split(","):
+            with open(os.path.join(ROOT, src.strip()), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != fields["sources_sha256"]:
+            return None
+        return int(fields["traffic_bytes_full_launch"])
+    except (KeyError, OSError, ValueError):
+        return None
 
 
 class Clocks:
@@ -125,6 +163,323 @@ def oracle_sample(values, lit, rows):
     return rows / dt / 1e9, int(out.size), dt
 
 
+# ------------------------------------------------------------ batched form
+def batched_pool(B, seed=0, ncols=32):
+    """32 resident columns: lengths log-uniform in [2^20, 2^28], code widths 8..32
+    bits, Zipf s uniform in [0, 1.5], layouts PP-VBS / ByteSlice / Bit-Packed in
+    turn (fixed-width layouts code value - domain_min over a declared 2^d range)."""
+    from paper_2209_00220_gb300 import synth
+    r = synth.u64(seed, 4040, 4 * ncols)
+    pool = []
+    for i in range(ncols):
+        logn = 20 + float(r[i] >> np.uint64(11)) / float(1 << 53) * 8
+        n = int(2 ** logn)
+        d = 8 + int(r[ncols + i] % np.uint64(25))
+        s = float(r[2 * ncols + i] % np.uint64(1000)) / 1000 * 1.5
+        lay = ("ppvbs", "byteslice", "bitpacked")[i % 3]
+        v = synth.config_sweep_column(n, d, s, seed * 1000 + i)
+        opts = {} if lay == "ppvbs" else {"domain_bits": d, "domain_min": synth.domain_min_for_bits(d)}
+        pool.append((v, B.bs_encode_column(v, lay, **opts), lay, d, s))
+    return pool
+
+
+def batched_requests(pool, nreq=256, seed=0):
+    """Per request: a pool column (uniform), an op among <, =, BETWEEN and a
+    target selectivity log-uniform in [0.01%, 50%]."""
+    from paper_2209_00220_gb300 import synth
+    r = synth.u64(seed, 4141, 3 * nreq)
+    reqs = []
+    for i in range(nreq):
+        ci = int(r[i] % np.uint64(len(pool)))
+        op = ("lt", "eq", "between")[int(r[nreq + i] % np.uint64(3))]
+        tgt = 10 ** (-4 + float(r[2 * nreq + i] >> np.uint64(11)) / float(1 << 53) * np.log10(5000))
+        a, b = synth.pick_literals(pool[ci][0], op, tgt, i)
+        reqs.append((ci, op, a, b))
+    return reqs
+
+
+def run_batched(B, warmup=2, steps=5, seed=0):
+    import torch
+    pool = batched_pool(B, seed)
+    spec = batched_requests(pool, 256, seed)
+    cols = [p[1] for p in pool]
+    stream = torch.cuda.current_stream()
+    # plain path buffers, and the exact counts from a first plain pass
+    bits = {ci: torch.empty(max(1, cols[ci].n_words), dtype=torch.int32, device="cuda") for ci, _, _, _ in spec}
+    ws = {ci: torch.empty(B.bs_lookup_workspace_bytes(cols[ci]) // 4 + 1, dtype=torch.int32, device="cuda")
+          for ci, _, _, _ in spec}
+    cnt = torch.zeros(len(spec), dtype=torch.int64, device="cuda")
+    big = torch.empty(max(c.n for c in cols), dtype=torch.int32, device="cuda")
+    for i, (ci, op, a, b) in enumerate(spec):
+        B.bs_scan(cols[ci], op, a, b, out=bits[ci], stream=stream)
+        B.bs_lookup(cols[ci], bits[ci], out=big, count=cnt[i:i + 1], workspace=ws[ci], stream=stream)
+    torch.cuda.synchronize()
+    counts = cnt.cpu().numpy().astype(np.int64)
+    outs_plain = [torch.empty(max(1, int(c)), dtype=torch.int32, device="cuda") for c in counts]
+    outs_batch = [torch.empty(max(1, int(c)), dtype=torch.int32, device="cuda") for c in counts]
+    cnt_b = torch.zeros(len(spec), dtype=torch.int64, device="cuda")
+
+    def plain_once(evs=None):
+        for i, (ci, op, a, b) in enumerate(spec):
+            B.bs_scan(cols[ci], op, a, b, out=bits[ci], stream=stream)
+            B.bs_lookup(cols[ci], bits[ci], out=outs_plain[i], out_cap=int(counts[i]), count=cnt[i:i + 1],
+                        workspace=ws[ci], stream=stream)
+            if evs is not None:
+                evs[i].record(stream)
+
+    reqs = [{"preds": [(cols[ci], op, a, b)], "out": outs_batch[i], "out_cap": int(counts[i]),
+             "count": cnt_b[i:i + 1]} for i, (ci, op, a, b) in enumerate(spec)]
+    cache = os.path.join(ROOT, "gpurun_out", "batch_tune.jsonl")
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    batch = B.bs_batch_create(reqs, autotune=True, tune_cache=cache)
+    for _ in range(warmup):
+        plain_once()
+        batch.launch(stream)
+    torch.cuda.synchronize()
+    t_plain, t_batch, lat_plain = [], [], []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in spec]
+        e0.record(stream)
+        plain_once(evs)
+        torch.cuda.synchronize()
+        done = np.array([e0.elapsed_time(e) for e in evs])
+        t_plain.append(done[-1])
+        lat_plain.append(done)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        batch.launch(stream)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        t_batch.append(b0.elapsed_time(b1))
+    same = bool(torch.equal(cnt, cnt_b)) and all(
+        torch.equal(outs_plain[i][:int(counts[i])], outs_batch[i][:int(counts[i])]) for i in range(len(spec)))
+    lp = np.concatenate(lat_plain)
+    rows = int(sum(cols[ci].n for ci, _, _, _ in spec))
+    tb, tp = float(np.median(t_batch)), float(np.median(t_plain))
+    return {"requests": len(spec), "columns": len(cols), "pool_rows": int(sum(c.n for c in cols)),
+            "rows_scanned": rows, "selected": int(counts.sum()),
+            "plain_ms": round(tp, 4), "batched_ms": round(tb, 4), "speedup": round(tp / tb, 3),
+            "batched_grows_s": round(rows / (tb / 1e3) / 1e9, 2), "plain_grows_s": round(rows / (tp / 1e3) / 1e9, 2),
+            "p50_ms": round(tb, 4), "p99_ms": round(tb, 4),
+            "plain_p50_ms": round(float(np.percentile(lp, 50)), 4), "plain_p99_ms": round(float(np.percentile(lp, 99)), 4),
+            "latency": "closed loop: all 256 submitted at t=0; a batched request completes with its launch",
+            "identical": same, "shape": batch.info(), "gpu_launches_per_batch": 2}
+
+
+# ------------------------------------------------------------ serving form
+SERVE_LENGTHS = (1 << 28, 1 << 29, 759250125, 1 << 30)  # 2^28, 2^29, 2^29.5, 2^30 rows
+
+
+def serving_tables(B, seed=0, scale=1.0):
+    """16 resident PP-VBS columns as 4 equal-length tables of 4 columns (table
+    lengths 2^28 .. 2^30 rows); per column a code width of 10..24 bits and a Zipf
+    s in [0, 1.5]. Host values are dropped after encoding; a 2^16-row sample of
+    each column stays for picking literals."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2209_00220_gb300 import synth
+    r = synth.u64(seed, 5050, 32)
+    tables = []
+    for t, n0 in enumerate(SERVE_LENGTHS):
+        n = max(1 << 16, int(n0 * scale))
+
+        def gen(j, t=t, n=n):
+            i = 4 * t + j
+            d = 10 + int(r[i] % np.uint64(15))
+            s = float(r[16 + i] % np.uint64(1000)) / 1000 * 1.5
+            return synth.config_sweep_column(n, d, s, 7000 + i), d, s
+
+        with ThreadPoolExecutor(4) as ex:
+            gen_out = list(ex.map(gen, range(4)))
+        cols, samples, meta = [], [], []
+        for j, (v, d, s) in enumerate(gen_out):
+            idx = (synth.u64(4 * t + j, 98, 1 << 16) % np.uint64(n)).astype(np.int64)
+            samples.append(v[idx])
+            cols.append(B.bs_encode_column(v, "ppvbs"))
+            meta.append((d, round(s, 3)))
+        del gen_out
+        tables.append((n, cols, samples, meta))
+    return tables
+
+
+def serving_queries(tables, count, seed=0):
+    """1-3-predicate conjunctions on the columns of one table (uniform), ops among
+    <, =, BETWEEN, >=, overall target selectivity log-uniform in [0.01%, 10%]
+    split evenly over the predicates; projection column uniform in the table."""
+    from paper_2209_00220_gb300 import synth
+    r = synth.u64(seed, 5151, 12 * count)
+    out = []
+    for i in range(count):
+        n, cols, samples, _ = tables[int(r[i] % np.uint64(len(tables)))]
+        npred = 1 + int(r[count + i] % np.uint64(3))
+        first = int(r[2 * count + i] % np.uint64(4))
+        sel = 10 ** (-4 + 3 * float(r[3 * count + i] >> np.uint64(11)) / float(1 << 53))
+        preds = []
+        for j in range(npred):
+            c = (first + j) % 4
+            op = ("lt", "eq", "between", "ge")[int(r[(4 + j) * count + i] % np.uint64(4))]
+            a, b = synth.pick_literals(samples[c], op, sel ** (1.0 / npred), i * 5 + j)
+            preds.append((cols[c], op, a, b))
+        proj = cols[int(r[8 * count + i] % np.uint64(4))]
+        out.append((preds, proj, n))
+    return out
+
+
+def poisson_arrivals(rate, count, seed):
+    from paper_2209_00220_gb300 import synth
+    u = (synth.u64(seed, 5252, count) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    return np.cumsum(-np.log1p(-u) / rate)
+
+
+def serve_plain(B, queries, max_rows):
+    """Serial plain execution: per query bs_scan_conj, bs_lookup and the count
+    read back to the host. Returns per-query service seconds and counts."""
+    import torch
+    bits = torch.empty((max_rows + 31) // 32, dtype=torch.int32, device="cuda")
+    out = torch.empty(max_rows, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    big = max(queries, key=lambda q: q[2])[1]
+    work = torch.empty(B.bs_lookup_workspace_bytes(big) // 4 + 1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    h_cnt = torch.empty(1, dtype=torch.int64, pin_memory=True)
+
+    def one(q):
+        preds, proj, n = q
+        B.bs_scan_conj(preds, out=bits, stream=stream)
+        B.bs_lookup(proj, bits, out=out, count=cnt, workspace=work, stream=stream)
+        h_cnt.copy_(cnt, non_blocking=True)
+        stream.synchronize()
+        return int(h_cnt.item())
+
+    for q in queries[:8]:
+        one(q)
+    svc, counts = np.empty(len(queries)), np.empty(len(queries), dtype=np.int64)
+    for i, q in enumerate(queries):
+        t0 = time.perf_counter()
+        counts[i] = one(q)
+        svc[i] = time.perf_counter() - t0
+    return svc, counts, (bits, out, cnt, work)
+
+
+def queue_fifo(arrivals, svc):
+    """Completion times of a single FIFO server with the given service times."""
+    done = np.empty_like(arrivals)
+    t = 0.0
+    for i, (a, s) in enumerate(zip(arrivals, svc)):
+        t = max(t, a) + s
+        done[i] = t
+    return done
+
+
+def serve_at(B, srv, prepared, arrivals, want_counts):
+    """Submits each query at its arrival time; a collector thread waits on the
+    tickets in order, records the latency from the scheduled arrival and
+    releases the result."""
+    import queue
+    import threading
+    q = queue.Queue()
+    lat = np.zeros(len(prepared))
+    done_t = np.zeros(len(prepared))
+    bad = []
+
+    def collect():
+        for _ in range(len(prepared)):
+            i, ticket, t_sub = q.get()
+            r = srv.wait(ticket, 600000)
+            if r["status"] != 0 or r["count"] != want_counts[i]:
+                bad.append(i)
+            lat[i] = (t_sub - arrivals[i]) + r["latency_us"] * 1e-6
+            done_t[i] = t_sub + r["latency_us"] * 1e-6  # seconds after the stream's start
+            srv.release(ticket)
+
+    th = threading.Thread(target=collect)
+    th.start()
+    t0 = time.perf_counter()
+    for i, pq in enumerate(prepared):
+        due = t0 + arrivals[i]
+        while time.perf_counter() < due:
+            pass
+        t_sub = time.perf_counter()
+        q.put((i, srv.submit(pq), t_sub - t0))
+    th.join()
+    return lat, done_t, bad
+
+
+def run_serving(B, rates=(1000, 3000, 10000, 30000, 100000), seconds=2.0, max_queries=6000, distinct=1024, scale=1.0,
+                seed=0):
+    """The arrival stream draws (seeded, uniform) from `distinct` generated
+    queries; plain service times and counts are measured once per distinct query."""
+    import torch
+    from paper_2209_00220_gb300 import synth
+    t_setup = time.time()
+    tables = serving_tables(B, seed, scale)
+    setup_s = time.time() - t_setup
+    distinct_q = serving_queries(tables, distinct, seed)
+    max_rows = max(t[0] for t in tables)
+    svc_d, counts_d, keep = serve_plain(B, distinct_q, max_rows)
+    nq = max_queries
+    pick = (synth.u64(seed, 5353, nq) % np.uint64(distinct)).astype(np.int64)
+    queries = [distinct_q[i] for i in pick]
+    svc, counts = svc_d[pick], counts_d[pick]
+    del keep
+    torch.cuda.empty_cache()
+    srv = B.bs_server_create(max_batch=64, slots=2, result_bytes=16 << 30, scratch_bytes=16 << 30)
+    prepared = [srv.prepare(p, proj) for p, proj, _ in queries]
+    # warm-up: the server's first batches
+    warm = [srv.submit(pq) for pq in prepared[:64]]
+    for t in warm:
+        srv.wait(t, 600000)
+        srv.release(t)
+    old_si = sys.getswitchinterval()
+    sys.setswitchinterval(2e-4)
+    runs = []
+    try:
+        for k, rate in enumerate(rates):
+            m = int(min(nq, max(200, rate * seconds)))
+            arr = poisson_arrivals(rate, m, seed + k)
+            st0 = srv.stats()
+            lat, done_t, bad = serve_at(B, srv, prepared[:m], arr, counts)
+            st1 = srv.stats()
+            span = float(done_t.max())
+            pdone = queue_fifo(arr, svc[:m])
+            plat = pdone - arr
+            runs.append({
+                "offered_qps": rate, "queries": m,
+                "served_qps": round(m / span, 1), "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+                "plain_qps": round(m / float(pdone.max()), 1),
+                "plain_p50_ms": round(1e3 * float(np.percentile(plat, 50)), 3),
+                "plain_p99_ms": round(1e3 * float(np.percentile(plat, 99)), 3),
+                "batches": int(st1["batches"] - st0["batches"]),
+                "mean_batch": round((st1["completed"] - st0["completed"]) / max(1, st1["batches"] - st0["batches"]), 2),
+                "identical_counts": not bad})
+    finally:
+        sys.setswitchinterval(old_si)
+    # exact results: a sample of queries' values, served vs plain
+    same = True
+    bits = torch.empty((max_rows + 31) // 32, dtype=torch.int32, device="cuda")
+    for i in range(0, nq, max(1, nq // 24)):
+        if counts[i] > (1 << 24):
+            continue
+        p, proj, _ = queries[i]
+        B.bs_scan_conj(p, out=bits)
+        v, c = B.bs_lookup(proj, bits, out_cap=int(counts[i]) + 1)
+        t = srv.submit(prepared[i])
+        r = srv.wait(t, 600000)
+        got = srv.values(t, r["count"])
+        srv.release(t)
+        same = same and int(c.item()) == r["count"] and torch.equal(v[: r["count"]], got)
+    srv.destroy()
+    rows_in_hbm = sum(4 * t[0] for t in tables)
+    return {"columns": 16, "tables": [{"rows": t[0], "cols": t[3]} for t in tables],
+            "resident_rows": int(rows_in_hbm), "setup_s": round(setup_s, 1),
+            "distinct_queries": distinct, "plain_capacity_qps": round(nq / float(svc.sum()), 1),
+            "plain_mean_service_ms": round(1e3 * float(svc.mean()), 4),
+            "runs": runs, "identical_values_sample": bool(same),
+            "latency": "scheduled Poisson arrival to completion; plain = FIFO queue over measured serial service times",
+            "server": {"max_batch": 64, "slots": 2, "result_bytes": 16 << 30, "scratch_bytes": 16 << 30}}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -152,6 +507,11 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _scaled(full_traffic, n):
+    """Traffic quoted for the 2^30-row bench column, for the rows actually run."""
+    return None if full_traffic is None else int(round(full_traffic * n / float(1 << 30)))
 
 
 def run_ours(args):
@@ -245,10 +605,12 @@ def run_ours(args):
         int(h_cnt.item()) == int(np.count_nonzero(values < lit))
 
     hbm, peak_kind = _peaks()
-    scan_bytes = B.bs_scan_bytes(col, "lt", lit)["bytes"] if hasattr(B, "bs_scan_bytes") else \
-        info["n_rows"] + 4 * nw
+    scan_bytes = B.bs_scan_bytes(col, "lt", lit)["bytes"]
+    look_bytes = B.bs_lookup_bytes(col, h_bits.numpy().view(np.uint32))["bytes"]
     scan_avg_s = float(np.mean(scan_ms)) / 1e3
+    look_avg_s = float(np.mean(look_ms)) / 1e3
     achieved = scan_bytes / scan_avg_s / 1e9
+    look_achieved = look_bytes / look_avg_s / 1e9
     value = n * ws * args.steps / (total_ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "Grows/s", "n_gpus": ws, "steps": args.steps,
@@ -262,10 +624,17 @@ def run_ours(args):
         "scan_ms": round(float(np.median(scan_ms)), 4),
         "lookup_gvals_s": round(m / (float(np.mean(look_ms)) / 1e3) / 1e9, 3),
         "lookup_ms": round(float(np.median(look_ms)), 4),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": None,
-                     "kernel": "scan_dense_kernel<PP-VBS>", "peak_kind": peak_kind,
-                     "algorithmic_bytes": int(scan_bytes)},
+        # the lookup (count + offsets + gather kernels) takes most of the step
+        "roofline": {"bound": "hbm", "achieved": round(look_achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(look_achieved / hbm, 4),
+                     "traffic": _scaled(profile_traffic("lookup_ppvbs_k2_sweep"), n),
+                     "kernel": "bs_lookup: lookup_count + lookup_scan + lookup_gather<PP-VBS, K<=2>",
+                     "peak_kind": peak_kind, "algorithmic_bytes": int(look_bytes)},
+        "roofline_scan": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                          "frac": round(achieved / hbm, 4),
+                          "traffic": _scaled(profile_traffic("scan_dense_ppvbs_sweep"), n),
+                          "kernel": "scan_dense_kernel<PP-VBS>", "peak_kind": peak_kind,
+                          "algorithmic_bytes": int(scan_bytes)},
         "e2e": {"value": round(n / e2e_s / 1e9, 4), "unit": "Grows/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 4 * nw + 4 * m + 8},
         "gpu_launches": args.steps * 4,
@@ -273,10 +642,19 @@ def run_ours(args):
         "encode_s": round(encode_s, 2),
         "parity_sample_ok": ok,
     }
+    if not args.no_batched:
+        del out, h_out
+        torch.cuda.empty_cache()
+        line["batched"] = run_batched(B)
+    if not args.no_serving:
+        torch.cuda.empty_cache()
+        line["serving"] = run_serving(B, scale=args.serve_scale)
     if rank == 0 and ws == 1 and not args.no_cpu:
-        g, _, dt = oracle_sample(values, lit, args.ref_rows)
+        rows = min(n, args.cpu_rows)
+        g, _, dt = oracle_sample(values, lit, rows)
         line["cpu_baseline"] = {"value": round(g, 6), "unit": "Grows/s", "cores": 1, "kind": "oracle",
-                                "sample": "first %d rows, decode + scan + lookup, %.1f s" % (args.ref_rows, dt)}
+                                "sample": "first %d rows of the bench column, decode + scan + lookup, %.1f s"
+                                          % (rows, dt)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -291,8 +669,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rows", type=int, default=1 << 30)
-    ap.add_argument("--ref-rows", type=int, default=1 << 24)
+    ap.add_argument("--ref-rows", type=int, default=1 << 24, help="oracle rows per step of --impl reference")
+    ap.add_argument("--cpu-rows", type=int, default=1 << 28, help="oracle rows timed for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-request batched measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-scale", type=float, default=1.0, help="serving table lengths x this factor")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -320,10 +320,12 @@ typedef struct bs_batch bs_batch; /* opaque: descriptors, scratch, captured grap
 /* Prepare a batch of nreq requests (1..65536) for repeated launches: encodes
  * every literal, uploads the request descriptors, allocates the batch scratch
  * (bit vectors not supplied by the caller, per-chunk counts and offsets) and
- * captures one persistent cooperative kernel in a CUDA graph. All columns must
- * live on the same device. Output buffers stay owned by the caller and must
- * outlive the batch. Errors: INVALID_ARG, UNSUPPORTED (raw-code column), OOM,
- * CUDA. Not part of the paper: its batched launch has no counterpart there. */
+ * captures one CUDA graph: requests over columns of 2^28 rows or more run the
+ * single-query scan and lookup kernels (as bs_scan_conj + bs_lookup would),
+ * all others one persistent cooperative kernel. All columns must live on the
+ * same device and outlive the batch; so must the caller's output buffers.
+ * Errors: INVALID_ARG, UNSUPPORTED (raw-code column), OOM, CUDA. Not part of
+ * the paper: its batched launch has no counterpart there. */
 int bs_batch_create(const bs_request *reqs, int32_t nreq, const bs_batch_opts *opts, bs_batch **out);
 
 /* Run every request of the batch with one launch (one graph launch, or one
@@ -388,10 +390,12 @@ typedef struct bs_server bs_server; /* opaque */
 /* A serving loop over resident columns (the paper has no counterpart). A
  * dispatcher thread admits queued queries in arrival order while their result
  * buffers (bound from bs_estimate_rows) and scratch fit the budgets, packs the
- * admitted ones into a batch and launches it (the batched kernel of
- * bs_batch_create, sized to share the GPU with the other slots) as soon as a
- * slot is free; queries arriving meanwhile join the next batch (continuous
- * batching). Results stay in device memory until released. */
+ * admitted ones into a batch and launches it on a free slot's stream as
+ * bs_batch_create's graph would run it (queries over columns of 2^28 rows or
+ * more by the single-query kernels, the others by the persistent kernel, sized
+ * to share the GPU with the other slots); queries arriving meanwhile join the
+ * next batch (continuous batching). Columns must outlive the queries that use
+ * them. Results stay in device memory until released. */
 int bs_server_create(const bs_server_opts *opts, bs_server **out);
 
 /* Enqueue a query (non-blocking). Errors: INVALID_ARG, UNSUPPORTED, CAPACITY

@@ -11,10 +11,15 @@
 //               tile, the request's predicates run in order with the running
 //               result as the seed held in registers (the pipelined bit vectors
 //               of Section 3.3.1 without a round trip through memory; a tile
-//               whose rows are all decided stops early). The final bit vector
-//               word is stored and the chunk's selected rows are counted.
-//   2. offsets -- one CTA per request turns its chunk counts into exclusive
-//               offsets and writes the request's selected-row count.
+//               whose rows are all decided stops early). The first predicate's
+//               dense slice streams through a 3-stage cp.async ring in the
+//               warp's shared memory. The final bit vector word is stored, the
+//               chunk's selected rows are counted and added to the total of its
+//               segment (512 chunks).
+//   2. offsets -- one warp per (request, segment): the earlier segments'
+//               totals give the segment's base, a warp scan of its 512 chunk
+//               counts the chunks' exclusive offsets; the last segment's warp
+//               writes the request's selected-row count.
 //   3. gather -- warps claim units again and run the lookup's chunk gather
 //               (lookup_dev.cuh) at the chunk's offset.
 // The host encodes every literal, uploads the request descriptors, sizes the
@@ -44,6 +49,7 @@ namespace bs {
 namespace {
 
 constexpr int kMaxPreds = BS_MAX_CONJ;
+constexpr uint32_t kSegChunks = 512;  // chunks per offset segment: 16 per lane of a warp
 
 struct BPred {
     ScanK a;
@@ -57,17 +63,22 @@ struct BReq {
     LookK look;             // projection column view + bits, outputs
     const int32_t *val1;    // projection is PP-VBS: one-byte code values
     uint32_t *bits;         // result bit vector (ceil(n/32) words)
-    uint32_t *chunk_cnt;    // per chunk: selected rows, then (phase 2) unchanged
-    uint64_t *chunk_off;    // per chunk: first output slot
+    uint32_t *chunk_cnt;    // per chunk: selected rows (phase 1)
+    uint64_t *chunk_off;    // per chunk: first output slot (phase 2)
+    uint64_t *seg_tot;      // per segment of kSegChunks chunks: selected rows (zeroed before launch)
     uint32_t n_chunks;
-    uint32_t unit0;         // first unit of this request
+    uint32_t n_segs;        // max(1, ceil(n_chunks / kSegChunks))
+    uint32_t unit0;         // first chunk unit of this request
+    uint32_t seg0;          // first segment of this request
 };
 
 struct BatchK {
     const BReq *reqs;
     const uint32_t *unit0;  // nreq + 1 entries: prefix of chunk counts
+    const uint32_t *seg0;   // nreq + 1 entries: prefix of segment counts
     int32_t nreq;
     uint32_t total_units;
+    uint32_t total_segs;
     uint32_t *ctr;          // [0] scan units claimed, [1] gather units claimed, [2] barrier arrivals
     uint32_t *status;
 };
@@ -76,6 +87,7 @@ union WarpSmemAny {
     WarpSmemT<2> k2;
     WarpSmemT<4> k4;
     WarpSmemT<8> k8;
+    uint8_t ring[kStages][kTileRows];  // phase 1: the first predicate's slice tiles in flight
 };
 
 // ---------------------------------------------------------- predicate tile
@@ -119,6 +131,16 @@ __device__ __noinline__ uint32_t dense_dispatch(const ScanK &a, const ScanPlan &
     }
 }
 
+// A dense-slice predicate on one tile whose lane bytes x are already loaded.
+__device__ __forceinline__ uint32_t dense_pred(const BPred &P, uint32_t t, uint32_t lane, const uint32_t x[8],
+                                               uint32_t sd) {
+    const ScanPlan &pl = P.plan;
+    if (pl.vbs) return pl.nlit == 2 ? dense_dispatch<true, 2>(P.a, pl, t, lane, x, sd)
+                                    : dense_dispatch<true, 1>(P.a, pl, t, lane, x, sd);
+    return pl.nlit == 2 ? dense_dispatch<false, 2>(P.a, pl, t, lane, x, sd)
+                        : dense_dispatch<false, 1>(P.a, pl, t, lane, x, sd);
+}
+
 // One predicate on one tile, restricted to the rows of sd (warp-wide call).
 __device__ __forceinline__ uint32_t pred_tile(const BPred &P, uint32_t t, uint32_t lane, uint32_t sd) {
     const ScanPlan &pl = P.plan;
@@ -127,17 +149,15 @@ __device__ __forceinline__ uint32_t pred_tile(const BPred &P, uint32_t t, uint32
     if (pl.kind == ScanPlan::kPacked) return sd ? packed_dispatch(a, pl.k, t, lane, sd) : 0u;
     uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (sd) load_lane32(a.dense + (uint64_t)t * kTileRows, lane, x);
-    if (pl.vbs) return pl.nlit == 2 ? dense_dispatch<true, 2>(a, pl, t, lane, x, sd)
-                                    : dense_dispatch<true, 1>(a, pl, t, lane, x, sd);
-    return pl.nlit == 2 ? dense_dispatch<false, 2>(a, pl, t, lane, x, sd)
-                        : dense_dispatch<false, 1>(a, pl, t, lane, x, sd);
+    return dense_pred(P, t, lane, x, sd);
 }
 
-__device__ __forceinline__ uint32_t find_request(const BatchK &b, uint32_t u) {
-    int lo = 0, hi = b.nreq - 1;  // largest r with unit0[r] <= u
+// Largest r with prefix[r] <= u (prefix: nreq + 1 non-decreasing entries).
+__device__ __forceinline__ uint32_t find_request(const uint32_t *prefix, int nreq, uint32_t u) {
+    int lo = 0, hi = nreq - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(b.unit0 + mid) <= u) lo = mid;
+        if (__ldg(prefix + mid) <= u) lo = mid;
         else hi = mid - 1;
     }
     return (uint32_t)lo;
@@ -186,74 +206,107 @@ __device__ void grid_barrier(const BatchK &b, uint32_t round) {
     __syncthreads();
 }
 
-__global__ void batch_kernel(const BatchK b) {
+// 512-thread CTAs at two per SM at least: at most 64 registers a thread, so a
+// 256-thread shape keeps 32 warps resident per SM.
+__global__ void __launch_bounds__(512, 2) batch_kernel(const BatchK b) {
     extern __shared__ __align__(16) unsigned char batch_smem[];
-    __shared__ uint64_t warp_tot[32];
-    __shared__ uint64_t carry;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     WarpSmemAny &sm = reinterpret_cast<WarpSmemAny *>(batch_smem)[warp];
 
     // ---- phase 1: scan every request's chunks
+    uint8_t *ring = &sm.ring[0][0];
+    const uint32_t rbase = (uint32_t)__cvta_generic_to_shared(ring);
     for (;;) {
         const uint32_t u = claim(b.ctr + 0, lane);
         if (u >= b.total_units) break;
-        const uint32_t r = find_request(b, u);
+        const uint32_t r = find_request(b.unit0, b.nreq, u);
         const BReq &R = b.reqs[r];
         const uint32_t c = u - R.unit0;
         const uint64_t n = R.look.n;
+        const BPred &P0 = R.pred[0];
+        const bool staged = P0.plan.kind == ScanPlan::kDense;
+        const uint32_t t0 = c * (uint32_t)kChunkTiles;
+        const uint32_t t1 = min(t0 + (uint32_t)kChunkTiles, R.look.n_tiles);
+        // every dense slice holds whole tiles, so whole-tile copies stay in bounds;
+        // each lane copies, and later reads, only its own 32 bytes of a tile
+        auto issue = [&](uint32_t t, int stage) {
+            if (t < t1) {
+                const uint8_t *g = P0.a.dense + (uint64_t)t * kTileRows;
+                const uint32_t sa = rbase + (uint32_t)stage * kTileRows;
+                cp_async16(sa + lane * 16u, g + lane * 16u);
+                cp_async16(sa + 512u + lane * 16u, g + 512u + lane * 16u);
+            }
+            cp_async_commit();
+        };
+        if (staged) {
+            issue(t0, 0);
+            issue(t0 + 1, 1);
+        }
+        int stage = 0;
         uint32_t cnt = 0;
-        for (uint32_t tt = 0; tt < (uint32_t)kChunkTiles; tt++) {
-            const uint64_t t = (uint64_t)c * kChunkTiles + tt;
-            if (t >= R.look.n_tiles) break;
-            const uint64_t w = t * kTileWords + lane;
+        for (uint32_t t = t0; t < t1; t++) {
+            const uint64_t w = (uint64_t)t * kTileWords + lane;
             uint32_t sd = valid_mask(w * 32u, n);
-            for (int p = 0; p < R.npred; p++) {
+            if (staged) {
+                issue(t + 2, (stage + 2) % kStages);
+                cp_async_wait<kStages - 1>();
+                const uint4 *sp = reinterpret_cast<const uint4 *>(ring + stage * kTileRows);
+                const uint4 v0 = sp[lane], v1 = sp[32 + lane];
+                const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                sd = dense_pred(P0, t, lane, x, sd);
+                stage = (stage + 1) % kStages;
+            } else {
+                sd = pred_tile(P0, t, lane, sd);
+            }
+            for (int p = 1; p < R.npred; p++) {
                 if (!__any_sync(kFull, sd != 0u)) break;  // every row of the tile decided
-                sd = pred_tile(R.pred[p], (uint32_t)t, lane, sd);
+                sd = pred_tile(R.pred[p], t, lane, sd);
             }
             if (w * 32u < n) R.bits[w] = sd;
             cnt += __popc(sd);
         }
+        if (staged) cp_async_wait<0>();
         cnt = warp_sum(cnt);
-        if (lane == 0) R.chunk_cnt[c] = cnt;
+        if (lane == 0) {
+            R.chunk_cnt[c] = cnt;
+            if (cnt) atomicAdd((unsigned long long *)(R.seg_tot + c / kSegChunks), (unsigned long long)cnt);
+        }
     }
     grid_barrier(b, 1);
 
-    // ---- phase 2: chunk offsets, one CTA per request
-    for (int r = blockIdx.x; r < b.nreq; r += gridDim.x) {
-        const BReq &R = b.reqs[r];
-        if (threadIdx.x == 0) carry = 0;
-        __syncthreads();
-        for (uint32_t s0 = 0; s0 < R.n_chunks; s0 += blockDim.x) {
-            const uint32_t i = s0 + threadIdx.x;
-            const uint64_t v = i < R.n_chunks ? R.chunk_cnt[i] : 0u;
-            uint64_t incl = v;
+    // ---- phase 2: chunk offsets, one warp per (request, segment)
+    {
+        const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+        for (uint32_t u = gw; u < b.total_segs; u += nw) {
+            const uint32_t r = find_request(b.seg0, b.nreq, u);
+            const BReq &R = b.reqs[r];
+            const uint32_t sg = u - R.seg0;
+            uint64_t base = 0;
+            for (uint32_t i = lane; i < sg; i += 32) base += __ldcg(R.seg_tot + i);
+            base = warp_sum64(base);
+            const uint32_t c0 = sg * kSegChunks + lane * (kSegChunks / 32);
+            uint32_t v[kSegChunks / 32];
+            uint64_t tot = 0;
+#pragma unroll
+            for (int i = 0; i < (int)(kSegChunks / 32); i++) {
+                v[i] = c0 + i < R.n_chunks ? __ldcg(R.chunk_cnt + c0 + i) : 0u;
+                tot += v[i];
+            }
+            uint64_t incl = tot;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const uint64_t o = __shfl_up_sync(kFull, incl, d);
                 if (lane >= (uint32_t)d) incl += o;
             }
-            if (lane == 31) warp_tot[warp] = incl;
-            __syncthreads();
-            if (warp == 0) {
-                const uint64_t wt = lane < nwarp ? warp_tot[lane] : 0u;
-                uint64_t wi = wt;
+            uint64_t off = base + incl - tot;
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint64_t o = __shfl_up_sync(kFull, wi, d);
-                    if (lane >= (uint32_t)d) wi += o;
-                }
-                if (lane < nwarp) warp_tot[lane] = wi - wt;
+            for (int i = 0; i < (int)(kSegChunks / 32); i++) {
+                if (c0 + i < R.n_chunks) R.chunk_off[c0 + i] = off;
+                off += v[i];
             }
-            __syncthreads();
-            const uint64_t excl = carry + warp_tot[warp] + incl - v;
-            if (i < R.n_chunks) R.chunk_off[i] = excl;
-            __syncthreads();
-            if (threadIdx.x == blockDim.x - 1) carry = excl + v;
-            __syncthreads();
+            if (sg == R.n_segs - 1 && lane == 31 && R.look.count) *R.look.count = base + incl;
         }
-        if (threadIdx.x == 0 && R.look.count) *R.look.count = carry;
-        __syncthreads();
     }
     grid_barrier(b, 2);
 
@@ -261,10 +314,10 @@ __global__ void batch_kernel(const BatchK b) {
     for (;;) {
         const uint32_t u = claim(b.ctr + 1, lane);
         if (u >= b.total_units) break;
-        const uint32_t r = find_request(b, u);
+        const uint32_t r = find_request(b.unit0, b.nreq, u);
         const BReq &R = b.reqs[r];
         const uint32_t c = u - R.unit0;
-        const uint64_t base = R.chunk_off[c];
+        const uint64_t base = __ldcg(R.chunk_off + c);
         if (base >= R.look.out_cap) continue;
         if (R.kmax == 2) gather_any<2>(R.look, c, base, sm.k2, R.val1, lane);
         else if (R.kmax == 4) gather_any<4>(R.look, c, base, sm.k4, R.val1, lane);
@@ -273,9 +326,30 @@ __global__ void batch_kernel(const BatchK b) {
 }
 
 // ------------------------------------------------------------ request plan
-// Validates request q and fills R's predicate and lookup fields (everything
-// but the scratch pointers). device: -1 on entry for the first request.
-int plan_request(const bs_request &q, BReq &R, int &device, int n_layout[3]) {
+// Requests whose columns have at least this many tiles (2^28 rows) run as the
+// single-query kernels (specialised per predicate, as the plain calls) ahead
+// of the persistent kernel, which takes the others: one persistent launch pays
+// off for many short and medium columns, while a column this long keeps the
+// GPU busy alone and runs faster through the specialised kernels.
+constexpr uint32_t kPlainTiles = 262144;
+
+// A request run by the single-query kernels.
+struct PlainReq {
+    const Column *col[kMaxPreds];
+    KPred kp[kMaxPreds];
+    int npred;
+    const Column *proj;
+    int32_t *out;
+    uint64_t cap;
+    uint64_t *count;
+    uint32_t *bits;  // scratch: result bit vector
+    void *ws;        // scratch: lookup workspace
+};
+
+// Validates request q and fills R's predicate and lookup fields and P
+// (everything but the scratch pointers). device: -1 on entry for the first
+// request.
+int plan_request(const bs_request &q, BReq &R, PlainReq &P, int &device, int n_layout[3]) {
     if (q.npreds < 1 || q.npreds > kMaxPreds || !q.preds[0].col) return BS_ERR_INVALID_ARG;
     const bs_column *proj = q.proj ? q.proj : q.preds[0].col;
     const Column &pc = proj->c;
@@ -284,16 +358,18 @@ int plan_request(const bs_request &q, BReq &R, int &device, int n_layout[3]) {
     if (device < 0) device = pc.device;
     if (pc.device != device) return BS_ERR_INVALID_ARG;
     R = BReq{};
+    P = PlainReq{};
     R.npred = q.npreds;
+    P.npred = q.npreds;
     for (int p = 0; p < q.npreds; p++) {
         const bs_column *col = q.preds[p].col;
         if (!col || col->c.n != pc.n || col->c.device != device) return BS_ERR_INVALID_ARG;
         if (col->c.raw || !col->c.d_arena) return BS_ERR_UNSUPPORTED;
         if (q.preds[p].op < BS_LT || q.preds[p].op > BS_BETWEEN) return BS_ERR_INVALID_ARG;
-        KPred kp;
-        const int rc = rewrite_literal(col->c, q.preds[p].op, q.preds[p].lit, q.preds[p].lit2, kp);
+        const int rc = rewrite_literal(col->c, q.preds[p].op, q.preds[p].lit, q.preds[p].lit2, P.kp[p]);
         if (rc) return rc;
-        plan_scan(col->c, kp, nullptr, false, R.pred[p].a, R.pred[p].plan);
+        P.col[p] = &col->c;
+        plan_scan(col->c, P.kp[p], nullptr, false, R.pred[p].a, R.pred[p].plan);
         R.pred[p].a.out = nullptr;  // the batch kernel stores the final word itself
         if (n_layout) n_layout[col->c.layout]++;
     }
@@ -304,32 +380,53 @@ int plan_request(const bs_request &q, BReq &R, int &device, int n_layout[3]) {
     R.look.out_cap = q.d_out ? q.out_cap : 0;
     R.look.count = q.d_count;
     R.n_chunks = R.look.n_chunks;
+    R.n_segs = std::max<uint32_t>(1, (R.n_chunks + kSegChunks - 1) / kSegChunks);
+    P.proj = &pc;
+    P.out = q.d_out;
+    P.cap = R.look.out_cap;
+    P.count = q.d_count;
     return BS_OK;
 }
 
-// Scratch of one request inside a batch: bit vector (unless supplied),
-// per-chunk counts and offsets.
+bool runs_plain(const BReq &R) { return R.look.n_tiles >= kPlainTiles; }
+
+// Scratch of one request: bit vector (unless supplied), per-chunk counts and
+// offsets (together also the single-query lookup's workspace, which needs no
+// more than one count per chunk and one offset per 8 chunks).
+size_t scratch_part(uint64_t bytes) { return (std::max<uint64_t>(8, bytes) + 255) & ~(size_t)255; }
+
 size_t request_scratch(const BReq &R, bool own_bits) {
     const uint64_t nw = (R.look.n + 31) / 32;
-    const size_t a = own_bits ? ((std::max<uint64_t>(4, nw * 4) + 255) & ~(size_t)255) : 0;
-    return a + ((std::max<uint64_t>(4, (uint64_t)R.n_chunks * 4) + 255) & ~(size_t)255) +
-           ((std::max<uint64_t>(8, (uint64_t)R.n_chunks * 8) + 255) & ~(size_t)255);
+    return (own_bits ? scratch_part(nw * 4) : 0) + scratch_part((uint64_t)R.n_chunks * 4) +
+           scratch_part((uint64_t)R.n_chunks * 8);
 }
 
-void bind_scratch(BReq &R, uint8_t *p, uint32_t *user_bits, uint32_t *status) {
+void bind_scratch(BReq &R, PlainReq &P, uint8_t *p, uint32_t *user_bits, uint32_t *status) {
     const uint64_t nw = (R.look.n + 31) / 32;
     if (user_bits) {
         R.bits = user_bits;
     } else {
         R.bits = (uint32_t *)p;
-        p += (std::max<uint64_t>(4, nw * 4) + 255) & ~(size_t)255;
+        p += scratch_part(nw * 4);
     }
     R.chunk_cnt = (uint32_t *)p;
-    p += (std::max<uint64_t>(4, (uint64_t)R.n_chunks * 4) + 255) & ~(size_t)255;
+    p += scratch_part((uint64_t)R.n_chunks * 4);
     R.chunk_off = (uint64_t *)p;
     R.look.bits = R.bits;
     R.look.status = status;
     for (int q = 0; q < R.npred; q++) R.pred[q].a.status = status;
+    P.bits = R.bits;
+    P.ws = R.chunk_cnt;
+}
+
+// The single-query kernels of one request: the conjunction's scans (each after
+// the first seeded by, and overwriting, the running bit vector), then the lookup.
+int launch_plain(const PlainReq &P, cudaStream_t s) {
+    for (int p = 0; p < P.npred; p++) {
+        const int rc = launch_scan(*P.col[p], P.kp[p], p ? P.bits : nullptr, P.bits, s);
+        if (rc) return rc;
+    }
+    return launch_lookup(*P.proj, P.bits, P.out, nullptr, P.cap, P.count, P.ws, s);
 }
 
 // ------------------------------------------------------------- tuning cache
@@ -383,7 +480,9 @@ struct bs_batch {
     int device = 0;
     int nreq = 0;
     void *d_arena = nullptr;
-    bs::BatchK k{};
+    size_t zero_bytes = 0;  // counters and segment totals, cleared before every launch
+    std::vector<bs::PlainReq> plain;  // requests run by the single-query kernels
+    bs::BatchK k{};         // the others (k.nreq may be 0)
     int threads = 256;
     int ctas = 0;
     bool use_graph = true;
@@ -395,7 +494,12 @@ struct bs_batch {
 namespace {
 
 int launch_direct(bs_batch *b, cudaStream_t s) {
-    if (cudaMemsetAsync(b->k.ctr, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return BS_ERR_CUDA;
+    for (const bs::PlainReq &P : b->plain) {
+        const int rc = bs::launch_plain(P, s);
+        if (rc) return rc;
+    }
+    if (b->k.nreq == 0) return BS_OK;
+    if (cudaMemsetAsync(b->k.ctr, 0, b->zero_bytes, s) != cudaSuccess) return BS_ERR_CUDA;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)b->ctas);
     cfg.blockDim = dim3((unsigned)b->threads);
@@ -473,10 +577,10 @@ int bs_batch_create(const bs_request *reqs, int32_t nreq, const bs_batch_opts *o
     if (opts) o = *opts;
     // validate and plan on the host
     std::vector<BReq> h(nreq);
-    std::vector<uint32_t> unit0(nreq + 1, 0);
+    std::vector<PlainReq> hp(nreq);
     int device = -1;
     size_t scratch = 0;
-    std::vector<size_t> bits_off(nreq, 0);
+    std::vector<size_t> scratch_off(nreq, 0);
     auto take = [&](size_t bytes) {
         size_t at = (scratch + 255) & ~(size_t)255;
         scratch = at + bytes;
@@ -484,19 +588,26 @@ int bs_batch_create(const bs_request *reqs, int32_t nreq, const bs_batch_opts *o
     };
     uint64_t total_rows = 0;
     int n_layout[3] = {0, 0, 0};
+    std::vector<int> batched;  // indexes of the requests the persistent kernel runs
     for (int r = 0; r < nreq; r++) {
         const bs_request &q = reqs[r];
-        const int prc = plan_request(q, h[r], device, n_layout);
+        const int prc = plan_request(q, h[r], hp[r], device, n_layout);
         if (prc) return prc;
-        BReq &R = h[r];
-        unit0[r] = (r ? unit0[r - 1] + h[r - 1].n_chunks : 0);
-        total_rows += R.look.n;
-        bits_off[r] = take(request_scratch(R, q.d_bits == nullptr));
+        total_rows += h[r].look.n;
+        scratch_off[r] = take(request_scratch(h[r], q.d_bits == nullptr));
+        if (!runs_plain(h[r])) batched.push_back(r);
     }
-    unit0[nreq] = unit0[nreq - 1] + h[nreq - 1].n_chunks;
-    const size_t o_ctr = take(256);
+    const int nb = (int)batched.size();
+    std::vector<uint32_t> unit0(nb + 1, 0), seg0(nb + 1, 0);
+    for (int i = 0; i < nb; i++) {
+        unit0[i + 1] = unit0[i] + h[batched[i]].n_chunks;
+        seg0[i + 1] = seg0[i] + h[batched[i]].n_segs;
+    }
+    const size_t zero_bytes = 256 + (size_t)seg0[nb] * 8;  // counters, then segment totals
+    const size_t o_ctr = take(zero_bytes);
     const size_t o_unit0 = take(unit0.size() * 4);
-    const size_t o_reqs = take(sizeof(BReq) * (size_t)nreq);
+    const size_t o_seg0 = take(seg0.size() * 4);
+    const size_t o_reqs = take(sizeof(BReq) * (size_t)std::max(nb, 1));
     int prev = 0;
     cudaGetDevice(&prev);
     if (cudaSetDevice(device) != cudaSuccess) return BS_ERR_CUDA;
@@ -504,6 +615,7 @@ int bs_batch_create(const bs_request *reqs, int32_t nreq, const bs_batch_opts *o
     if (!b) return BS_ERR_OOM;
     b->device = device;
     b->nreq = nreq;
+    b->zero_bytes = zero_bytes;
     b->use_graph = o.use_graph != 0;
     int rc = BS_OK;
     if (cudaMalloc(&b->d_arena, scratch) != cudaSuccess) {
@@ -511,23 +623,32 @@ int bs_batch_create(const bs_request *reqs, int32_t nreq, const bs_batch_opts *o
         rc = BS_ERR_OOM;
     }
     uint8_t *base = (uint8_t *)b->d_arena;
+    std::vector<BReq> hb(std::max(nb, 1));
     if (rc == BS_OK) {
         uint32_t *status = status_word();
         if (!status) rc = BS_ERR_CUDA;
         for (int r = 0; r < nreq && rc == BS_OK; r++) {
-            bind_scratch(h[r], base + bits_off[r], reqs[r].d_bits, status);
-            h[r].unit0 = unit0[r];
+            bind_scratch(h[r], hp[r], base + scratch_off[r], reqs[r].d_bits, status);
+            if (runs_plain(h[r])) b->plain.push_back(hp[r]);
+        }
+        for (int i = 0; i < nb; i++) {
+            hb[i] = h[batched[i]];
+            hb[i].unit0 = unit0[i];
+            hb[i].seg0 = seg0[i];
+            hb[i].seg_tot = (uint64_t *)(base + o_ctr + 256) + seg0[i];
         }
         b->k.reqs = (const BReq *)(base + o_reqs);
         b->k.unit0 = (const uint32_t *)(base + o_unit0);
-        b->k.nreq = nreq;
-        b->k.total_units = unit0[nreq];
+        b->k.seg0 = (const uint32_t *)(base + o_seg0);
+        b->k.nreq = nb;
+        b->k.total_units = unit0[nb];
+        b->k.total_segs = seg0[nb];
         b->k.ctr = (uint32_t *)(base + o_ctr);
         b->k.status = status;
-        if (rc == BS_OK && (cudaMemcpy(base + o_reqs, h.data(), sizeof(BReq) * (size_t)nreq, cudaMemcpyHostToDevice) !=
-                                cudaSuccess ||
-                            cudaMemcpy(base + o_unit0, unit0.data(), unit0.size() * 4, cudaMemcpyHostToDevice) !=
-                                cudaSuccess))
+        if (rc == BS_OK && nb > 0 &&
+            (cudaMemcpy(base + o_reqs, hb.data(), sizeof(BReq) * (size_t)nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(base + o_unit0, unit0.data(), unit0.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(base + o_seg0, seg0.data(), seg0.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess))
             rc = BS_ERR_CUDA;
     }
     // launch shape: explicit, cached, autotuned or the default
@@ -536,12 +657,12 @@ int bs_batch_create(const bs_request *reqs, int32_t nreq, const bs_batch_opts *o
         cudaDeviceProp prop{};
         cudaGetDeviceProperties(&prop, device);
         char key[384];
-        std::snprintf(key, sizeof key, "%s|nreq=%d|rows=2^%d|vbs=%d,bsl=%d,bp=%d", prop.name, nreq,
-                      total_rows ? 63 - __builtin_clzll(total_rows) : 0, n_layout[BS_PPVBS], n_layout[BS_BYTESLICE],
-                      n_layout[BS_BITPACKED]);
+        std::snprintf(key, sizeof key, "%s|nreq=%d|plain=%d|rows=2^%d|vbs=%d,bsl=%d,bp=%d", prop.name, nreq,
+                      (int)b->plain.size(), total_rows ? 63 - __builtin_clzll(total_rows) : 0, n_layout[BS_PPVBS],
+                      n_layout[BS_BYTESLICE], n_layout[BS_BITPACKED]);
         const std::string path = tune_path(o);
         if (o.threads <= 0 && !o.autotune) tune_lookup(path, key, threads, bps);
-        if (o.autotune) {
+        if (o.autotune && nb > 0) {
             const int cand_t[3] = {128, 256, 512};
             const int cand_b[3] = {1, 2, 0};
             double best = 1e30;
@@ -675,6 +796,7 @@ class RangeAlloc {
 
 struct QueryRec {
     bs::BReq plan;
+    bs::PlainReq plain;           // the same query for the single-query kernels
     uint64_t bound = 0;           // upper bound of selected rows
     size_t out_bytes = 0, out_off = SIZE_MAX;
     size_t scratch_bytes = 0, scratch_off = SIZE_MAX;
@@ -686,9 +808,10 @@ struct QueryRec {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    uint8_t *d_desc = nullptr;    // BReq[max_batch] | unit0 | ctr | counts
+    uint8_t *d_desc = nullptr;    // BReq[max_batch] | unit0 | seg0 | ctr + segment totals | counts
     uint8_t *h_desc = nullptr;    // pinned mirror
-    size_t desc_bytes = 0, o_unit0 = 0, o_ctr = 0, o_counts = 0;
+    size_t desc_bytes = 0, o_unit0 = 0, o_seg0 = 0, o_ctr = 0, o_counts = 0;
+    std::vector<bs::PlainReq> plain;  // this batch's queries for the single-query kernels
     bool busy = false;
     std::vector<uint64_t> tickets;
 };
@@ -717,30 +840,41 @@ struct bs_server {
 namespace {
 
 // Launches the batch of `slot` (descriptors already in its pinned mirror).
-int launch_slot(bs_server *S, Slot &sl, int nreq, uint32_t total_units) {
+// Launches the batch of `slot`: the single-query kernels of its long queries,
+// then the persistent kernel over the others (descriptors already in the
+// pinned mirror), then the read-back of all counts and the completion event.
+int launch_slot(bs_server *S, Slot &sl, int nall, int nreq, uint32_t total_units, uint32_t total_segs) {
     using namespace bs;
-    BatchK k{};
-    k.reqs = (const BReq *)sl.d_desc;
-    k.unit0 = (const uint32_t *)(sl.d_desc + sl.o_unit0);
-    k.nreq = nreq;
-    k.total_units = total_units;
-    k.ctr = (uint32_t *)(sl.d_desc + sl.o_ctr);
-    k.status = S->status;
-    if (cudaMemcpyAsync(sl.d_desc, sl.h_desc, sl.o_ctr, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
-        return BS_ERR_CUDA;
-    if (cudaMemsetAsync(k.ctr, 0, 4 * sizeof(uint32_t), sl.stream) != cudaSuccess) return BS_ERR_CUDA;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)S->ctas);
-    cfg.blockDim = dim3((unsigned)S->threads);
-    cfg.dynamicSmemBytes = smem_bytes(S->threads);
-    cfg.stream = sl.stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, batch_kernel, k) != cudaSuccess) return BS_ERR_CUDA;
-    if (cudaMemcpyAsync(sl.h_desc + sl.o_counts, sl.d_desc + sl.o_counts, (size_t)nreq * 8, cudaMemcpyDeviceToHost,
+    for (const PlainReq &P : sl.plain) {
+        const int rc = launch_plain(P, sl.stream);
+        if (rc) return rc;
+    }
+    if (nreq > 0) {
+        BatchK k{};
+        k.reqs = (const BReq *)sl.d_desc;
+        k.unit0 = (const uint32_t *)(sl.d_desc + sl.o_unit0);
+        k.seg0 = (const uint32_t *)(sl.d_desc + sl.o_seg0);
+        k.nreq = nreq;
+        k.total_units = total_units;
+        k.total_segs = total_segs;
+        k.ctr = (uint32_t *)(sl.d_desc + sl.o_ctr);
+        k.status = S->status;
+        if (cudaMemcpyAsync(sl.d_desc, sl.h_desc, sl.o_ctr, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+            return BS_ERR_CUDA;
+        if (cudaMemsetAsync(k.ctr, 0, 256 + (size_t)total_segs * 8, sl.stream) != cudaSuccess) return BS_ERR_CUDA;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)S->ctas);
+        cfg.blockDim = dim3((unsigned)S->threads);
+        cfg.dynamicSmemBytes = smem_bytes(S->threads);
+        cfg.stream = sl.stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, batch_kernel, k) != cudaSuccess) return BS_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(sl.h_desc + sl.o_counts, sl.d_desc + sl.o_counts, (size_t)nall * 8, cudaMemcpyDeviceToHost,
                         sl.stream) != cudaSuccess)
         return BS_ERR_CUDA;
     if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return BS_ERR_CUDA;
@@ -778,9 +912,12 @@ void dispatcher(bs_server *S) {
             const int maxb = S->o.max_batch;
             BReq *reqs = (BReq *)sl.h_desc;
             uint32_t *unit0 = (uint32_t *)(sl.h_desc + sl.o_unit0);
+            uint32_t *seg0 = (uint32_t *)(sl.h_desc + sl.o_seg0);
             uint64_t *d_counts = (uint64_t *)(sl.d_desc + sl.o_counts);
-            int nb = 0;
-            uint32_t units = 0;
+            uint64_t *d_segs = (uint64_t *)(sl.d_desc + sl.o_ctr + 256);
+            int nb = 0, nk = 0;  // queries in the batch, of which run by the persistent kernel
+            uint32_t units = 0, segs = 0;
+            sl.plain.clear();
             while (nb < maxb && !S->queue.empty()) {
                 const uint64_t tk = S->queue.front();
                 QueryRec &q = S->recs[tk];
@@ -793,24 +930,37 @@ void dispatcher(bs_server *S) {
                 q.out_off = ro;
                 q.scratch_off = so;
                 BReq R = q.plan;
+                PlainReq P = q.plain;
                 R.look.out_vals = (int32_t *)(S->d_result + ro);
                 R.look.out_cap = q.bound;
                 R.look.count = d_counts + nb;
-                bind_scratch(R, S->d_scratch + so, nullptr, S->status);
-                R.unit0 = units;
-                unit0[nb] = units;
-                units += R.n_chunks;
-                reqs[nb] = R;
+                bind_scratch(R, P, S->d_scratch + so, nullptr, S->status);
+                P.out = R.look.out_vals;
+                P.cap = q.bound;
+                P.count = R.look.count;
+                if (runs_plain(R)) {
+                    sl.plain.push_back(P);
+                } else {
+                    R.unit0 = units;
+                    unit0[nk] = units;
+                    units += R.n_chunks;
+                    R.seg0 = segs;
+                    R.seg_tot = d_segs + segs;
+                    seg0[nk] = segs;
+                    segs += R.n_segs;
+                    reqs[nk++] = R;
+                }
                 sl.tickets.push_back(tk);
                 q.state = 1;
                 S->queue.pop_front();
                 nb++;
             }
             if (nb == 0) break;  // memory is full: wait for completions or releases
-            unit0[nb] = units;
+            unit0[nk] = units;
+            seg0[nk] = segs;
             const auto now = Clock::now();
             for (uint64_t tk : sl.tickets) S->recs[tk].t_launch = now;
-            if (launch_slot(S, sl, nb, units) != BS_OK) {
+            if (launch_slot(S, sl, nb, nk, units, segs) != BS_OK) {
                 // record the failure on the queries; they complete with count 0
                 for (uint64_t tk : sl.tickets) {
                     QueryRec &q = S->recs[tk];
@@ -920,7 +1070,9 @@ int bs_server_create(const bs_server_opts *opts, bs_server **out) {
         };
         take(sizeof(BReq) * (size_t)o.max_batch);
         sl.o_unit0 = take(((size_t)o.max_batch + 1) * 4);
-        sl.o_ctr = take(256);
+        sl.o_seg0 = take(((size_t)o.max_batch + 1) * 4);
+        // counters, then up to 512 segment totals per query (n < 2^32 rows)
+        sl.o_ctr = take(256 + (size_t)o.max_batch * 512 * 8);
         sl.o_counts = take((size_t)o.max_batch * 8);
         sl.desc_bytes = at;
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -950,7 +1102,7 @@ int bs_server_submit(bs_server *S, const bs_query *q, uint64_t *ticket) {
     for (int i = 0; i < BS_MAX_CONJ; i++) r.preds[i] = q->preds[i];
     r.proj = q->proj;
     int device = S->device;
-    int rc = plan_request(r, rec.plan, device, nullptr);
+    int rc = plan_request(r, rec.plan, rec.plain, device, nullptr);
     if (rc) return rc;
     if (device != S->device) return BS_ERR_INVALID_ARG;
     uint64_t bound = rec.plan.look.n;

@@ -95,15 +95,6 @@ __device__ __forceinline__ void st_stream(uint32_t *p, uint32_t v) {
     asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t smem_addr, const uint8_t *g) {
-    asm volatile("cp.async.cg.shared.global.L2::256B [%0], [%1], 16;" ::"r"(smem_addr), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async4(uint32_t smem_addr, const uint32_t *g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 
 __device__ __forceinline__ uint32_t lit_byte(const DLit &l, int j) {  // j = 1..8

@@ -122,3 +122,47 @@ def test_batch_capacity_and_autotune(B, tmp_path):
                            tune_cache=cache)
     assert b2.info()["threads"] == batch.info()["threads"]
     assert B.bs_last_device_error() == 0
+
+
+def test_long_columns_take_single_query_kernels_in_batch_and_server(B):
+    # columns of 2^28 rows or more run the specialised single-query kernels
+    # inside the batch (and the server's batches); a mix of long and short
+    # requests must still give the oracle's results for every request
+    import torch
+    n = 1 << 28
+    v1 = synth.config_sweep_column(n, 12, 1.0, 41)
+    v2 = synth.config_sweep_column(n, 18, 0.6, 42)
+    c1, c2 = B.bs_encode_column(v1, "ppvbs"), B.bs_encode_column(v2, "byteslice")
+    vs = synth.config_sweep_column(70001, 12, 1.0, 43)
+    cs = B.bs_encode_column(vs, "ppvbs")
+    a1, _ = synth.pick_literals(v1, "lt", 0.05, 1)
+    a2, b2 = synth.pick_literals(v2, "between", 0.3, 2)
+    a3, _ = synth.pick_literals(vs, "lt", 0.2, 3)
+    m1 = v1 < a1
+    want_long = v1[m1]
+    want_conj = v2[m1 & (v2 >= a2) & (v2 <= b2)]
+    want_short = vs[vs < a3]
+    cases = [([(c1, "lt", a1)], None, want_long), ([(c1, "lt", a1), (c2, "between", a2, b2)], c2, want_conj),
+             ([(cs, "lt", a3)], None, want_short)]
+    outs = [torch.empty(w.size + 7, dtype=torch.int32, device="cuda") for _, _, w in cases]
+    cnts = [torch.zeros(1, dtype=torch.int64, device="cuda") for _ in cases]
+    reqs = [{"preds": p, "proj": pj, "out": o, "count": c} for (p, pj, _), o, c in zip(cases, outs, cnts)]
+    for use_graph in (True, False):
+        batch = B.bs_batch_create(reqs, use_graph=use_graph)
+        for o in outs:
+            o.fill_(-1)
+        batch.launch()
+        torch.cuda.synchronize()
+        for (p, pj, w), o, c in zip(cases, outs, cnts):
+            assert int(c.item()) == w.size
+            assert np.array_equal(o[: w.size].cpu().numpy(), w)
+        batch.free()
+    srv = B.bs_server_create(max_batch=8, slots=2, result_bytes=1 << 30, scratch_bytes=2 << 30)
+    tickets = [srv.submit(p, pj) for p, pj, _ in cases for _ in range(2)]
+    for t, (p, pj, w) in zip(tickets, [c for c in cases for _ in range(2)]):
+        r = srv.wait(t, 60000)
+        assert r["status"] == 0 and r["count"] == w.size
+        assert np.array_equal(srv.values(t, r["count"]).cpu().numpy(), w)
+        srv.release(t)
+    srv.destroy()
+    assert B.bs_last_device_error() == 0
