@@ -387,22 +387,21 @@ __device__ __forceinline__ void row_code(const LookK &a, uint64_t row, uint64_t 
     }
 }
 
-// Dense PP-VBS tile whose codes have at most two bytes: every load that does
-// not depend on another (the lane's 32 BS_1 bytes, its M_2 word, its group's
-// BS_2 offset and the tile's BS_2 segment bounds) is issued in one round; the
-// segment words and then the two-byte decode table follow. Each lane walks its
+// Dense PP-VBS tile whose codes have at most two bytes: the off_2 entries of
+// the whole chunk come with the chunk (goff, seg_lo, seg_hi: the lane's group
+// offset and the tile's BS_2 segment bounds), so the lane's 32 BS_1 bytes, its
+// M_2 word and the tile's BS_2 segment are all loaded in one round; the
+// two-byte decode table follows. Each lane walks its
 // own selected rows in order and leaves a 16-bit key (first two code bytes) per
 // output slot; the warp then decodes the keys and stores them coalesced.
 __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint32_t sel, uint64_t out_base,
-                                                WarpSmemT<2> &sm, const int32_t *val1, uint32_t lane) {
-    // round 1: independent loads
+                                                uint32_t goff, uint32_t seg_lo, uint32_t seg_hi, WarpSmemT<2> &sm,
+                                                const int32_t *val1, uint32_t lane) {
+    // one round of independent loads: BS_1, M_2 and (below) the BS_2 segment
     const uint4 *src = reinterpret_cast<const uint4 *>(a.dense + t * kTileRows);
     const uint4 v0 = __ldg(src + lane), v1 = __ldg(src + 32 + lane);
     const bool has2 = a.K >= 2;
     const uint32_t m2 = has2 ? __ldg(a.mask[2] + t * kTileWords + lane) : 0u;
-    const uint32_t goff = has2 ? __ldg(a.off[2] + t * kGroupsPerTile + (lane >> 3)) : 0u;
-    const uint32_t seg_lo = has2 ? __ldg(a.off[2] + t * kGroupsPerTile) : 0u;
-    const uint32_t seg_hi = has2 ? __ldg(a.off[2] + t * kGroupsPerTile + kGroupsPerTile) : 0u;
     // ALU while they fly: output positions of this lane's rows
     const uint32_t cnt = __popc(sel);
     uint32_t incl = cnt;
@@ -419,7 +418,7 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
         const uint32_t v = __shfl_up_sync(kFull, inc2, d);
         if ((lane & 7u) >= (uint32_t)d) inc2 += v;
     }
-    // round 2: the tile's BS_2 bytes (contiguous)
+    // the tile's BS_2 bytes (contiguous)
     if (has2) {
         const uint32_t w0 = seg_lo >> 2, w1 = (seg_hi + 3) >> 2;
         const uint32_t *s32 = reinterpret_cast<const uint32_t *>(a.deep[2]);
@@ -428,29 +427,35 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
     }
     uint4 r0, r1;
     transpose_lane_bytes(v0, v1, r0, r1);
-    uint4 *dst = reinterpret_cast<uint4 *>(sm.dense + lane * 32u);
-    dst[0] = r0;
-    dst[1] = r1;
+    uint4 *rows = reinterpret_cast<uint4 *>(sm.dense + lane * 32u);
+    rows[0] = r0;
+    rows[1] = r1;
     __syncwarp();
     const uint8_t *seg = reinterpret_cast<const uint8_t *>(sm.seg) + (seg_lo & 3u);
     const uint32_t p2 = goff + inc2 - c2 - seg_lo;  // lane's first BS_2 byte, relative to the segment
+    // each selected row: its BS_1 byte and the BS_2 byte at its rank among the
+    // lane's two-byte rows, read unconditionally (the rank stays inside the
+    // staged segment) and kept only for rows whose M_2 bit is set
     uint32_t pos = incl - cnt, r = sel;
     while (r) {
         const uint32_t b = __ffs(r) - 1;
         r &= r - 1;
-        uint32_t key = (uint32_t)sm.dense[lane * 32u + b] << 8;
-        if ((m2 >> b) & 1u) key |= seg[p2 + __popc(m2 & ((1u << b) - 1u))];
-        sm.list[pos++] = (uint16_t)key;
+        const uint32_t c1 = sm.dense[lane * 32u + b];
+        const uint32_t c2b = seg[p2 + __popc(m2 & ((1u << b) - 1u))];
+        sm.list[pos++] = (uint16_t)((c1 << 8) | (((m2 >> b) & 1u) ? c2b : 0u));
     }
     __syncwarp();
-    // round 3: decode and store
-    for (uint32_t i0 = 0; i0 < total; i0 += 32 * kUnroll) {
+    // decode and store, 32-bit indexes inside the tile's output range
+    const uint64_t room = a.out_cap > out_base ? a.out_cap - out_base : 0;
+    const uint32_t lim = (uint32_t)(room < total ? room : total);
+    int32_t *dst = a.out_vals + out_base;
+    for (uint32_t i0 = 0; i0 < lim; i0 += 32 * kUnroll) {
         int32_t v[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; u++) {
             const uint32_t i = i0 + (uint32_t)u * 32u + lane;
             v[u] = 0;
-            if (i < total) {
+            if (i < lim) {
                 const uint32_t key = sm.list[i];
                 v[u] = (key & 0xFFu) ? __ldg(a.val2 + key) : val1[key >> 8];
             }
@@ -458,8 +463,7 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
 #pragma unroll
         for (int u = 0; u < kUnroll; u++) {
             const uint32_t i = i0 + (uint32_t)u * 32u + lane;
-            const uint64_t o = out_base + i;
-            if (i < total && o < a.out_cap) a.out_vals[o] = v[u];
+            if (i < lim) dst[i] = v[u];
         }
     }
     __syncwarp();
@@ -549,17 +553,47 @@ __device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_
         v += __shfl_xor_sync(kFull, v, 4);
         tcnt[i] = v;  // count of tile 4i + (lane >> 3)
     }
+    // PP-VBS, codes <= 2 bytes: the chunk's 65 off_2 entries, two per lane
+    // (entry e of the chunk at lane e / 2, the last one in every lane)
+    constexpr bool kK2 = LAYOUT == BS_PPVBS && !CODES && KMAX == 2;
+    uint32_t offa = 0, offb = 0, offz = 0;
+    if (kK2 && a.K >= 2) {
+        const uint64_t e0 = (uint64_t)c * kChunkTiles * kGroupsPerTile;
+        const uint64_t nent = (uint64_t)a.n_tiles * kGroupsPerTile + 1;
+        const uint64_t ea = e0 + 2 * lane;
+        offa = ea < nent ? __ldg(a.off[2] + ea) : 0u;
+        offb = ea + 1 < nent ? __ldg(a.off[2] + ea + 1) : 0u;
+        offz = e0 + 64 < nent ? __ldg(a.off[2] + e0 + 64) : 0u;
+    }
+    auto off_entry = [&](uint32_t e) -> uint32_t {  // warp-wide call; e <= 64
+        const uint32_t x = __shfl_sync(kFull, offa, (e >> 1) & 31u), y = __shfl_sync(kFull, offb, (e >> 1) & 31u);
+        return e >= 64u ? offz : ((e & 1u) ? y : x);
+    };
+    // lane i < 16 holds the selected-row count of tile i of the chunk
+    uint32_t tcl = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t v = __shfl_sync(kFull, tcnt[i], j * 8);
+            if (lane == (uint32_t)(4 * i + j)) tcl = v;
+        }
+    }
     for (int tt = 0; tt < kChunkTiles; tt++) {
-        const uint32_t tc = __shfl_sync(kFull, tcnt[tt >> 2], (tt & 3) * 8);
+        const uint32_t tc = __shfl_sync(kFull, tcl, tt);
         const uint64_t t = (uint64_t)c * kChunkTiles + tt;
         if (tc && t < a.n_tiles && base < a.out_cap) {
             const uint64_t w = t * kTileWords + lane;
             const uint32_t vm = valid_mask(w * 32u, a.n);
             const uint32_t sel = vm ? (__ldg(a.bits + w) & vm) : 0u;
-            if (LAYOUT == BS_PPVBS && !CODES && KMAX == 2 && tc >= kStageMin)
-                gather_dense_k2(a, t, sel, base, reinterpret_cast<WarpSmemT<2> &>(sm), val1, lane);
-            else
+            if (kK2 && tc >= kStageMin) {
+                const uint32_t e = (uint32_t)tt * kGroupsPerTile;
+                const uint32_t goff = off_entry(e + (lane >> 3));
+                const uint32_t lo = off_entry(e), hi = off_entry(e + kGroupsPerTile);
+                gather_dense_k2(a, t, sel, base, goff, lo, hi, reinterpret_cast<WarpSmemT<2> &>(sm), val1, lane);
+            } else {
                 gather_tile<LAYOUT, CODES, KMAX>(a, t, sel, base, sm, val1, lane);
+            }
         }
         base += tc;
     }
