@@ -173,9 +173,9 @@ template <int KMAX>
 __device__ __forceinline__ void gather_any(const LookK &a, uint32_t c, uint64_t base, WarpSmemT<KMAX> &sm,
                                            const int32_t *val1, uint32_t lane) {
     switch (a.layout) {
-    case BS_PPVBS: gather_chunk<BS_PPVBS, false, KMAX>(a, c, base, sm, val1, lane); break;
-    case BS_BYTESLICE: gather_chunk<BS_BYTESLICE, false, KMAX>(a, c, base, sm, val1, lane); break;
-    default: gather_chunk<BS_BITPACKED, false, KMAX>(a, c, base, sm, val1, lane); break;
+    case BS_PPVBS: gather_chunk<BS_PPVBS, false, KMAX, false>(a, c, base, sm, val1, lane); break;
+    case BS_BYTESLICE: gather_chunk<BS_BYTESLICE, false, KMAX, false>(a, c, base, sm, val1, lane); break;
+    default: gather_chunk<BS_BITPACKED, false, KMAX, false>(a, c, base, sm, val1, lane); break;
     }
 }
 

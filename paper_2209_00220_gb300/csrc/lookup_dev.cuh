@@ -473,7 +473,9 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
 // It reads the chunk's 512 bit vector words at once. A sparse chunk (at most
 // kSparseMax selected rows) lists its rows in shared memory and resolves them
 // all in parallel across lanes; a dense chunk goes tile by tile.
-template <int LAYOUT, bool CODES, int KMAX>
+// HOIST: dense two-byte PP-VBS chunks hold the chunk's off_2 entries in
+// registers (more registers); without it each dense tile loads its own.
+template <int LAYOUT, bool CODES, int KMAX, bool HOIST = true>
 __device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_t base, WarpSmemT<KMAX> &sm,
                                              const int32_t *val1, uint32_t lane) {
     const uint64_t nwords = (a.n + 31) / 32;
@@ -556,9 +558,10 @@ __device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_
     // PP-VBS, codes <= 2 bytes: the chunk's 65 off_2 entries, two per lane
     // (entry e of the chunk at lane e / 2, the last one in every lane)
     constexpr bool kK2 = LAYOUT == BS_PPVBS && !CODES && KMAX == 2;
+    constexpr bool kHoist = HOIST && kK2;
     uint32_t offa = 0, offb = 0, offz = 0;
-    if (kK2 && a.K >= 2) {
-        const uint64_t e0 = (uint64_t)c * kChunkTiles * kGroupsPerTile;
+    const uint64_t e0 = (uint64_t)c * kChunkTiles * kGroupsPerTile;
+    if (kHoist && a.K >= 2) {
         const uint64_t nent = (uint64_t)a.n_tiles * kGroupsPerTile + 1;
         const uint64_t ea = e0 + 2 * lane;
         offa = ea < nent ? __ldg(a.off[2] + ea) : 0u;
@@ -566,21 +569,26 @@ __device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_
         offz = e0 + 64 < nent ? __ldg(a.off[2] + e0 + 64) : 0u;
     }
     auto off_entry = [&](uint32_t e) -> uint32_t {  // warp-wide call; e <= 64
+        if (!kHoist) return a.K >= 2 ? __ldg(a.off[2] + e0 + e) : 0u;
         const uint32_t x = __shfl_sync(kFull, offa, (e >> 1) & 31u), y = __shfl_sync(kFull, offb, (e >> 1) & 31u);
         return e >= 64u ? offz : ((e & 1u) ? y : x);
     };
-    // lane i < 16 holds the selected-row count of tile i of the chunk
+    // hoisted: lane i < 16 holds the selected-row count of tile i of the chunk
     uint32_t tcl = 0;
+    if constexpr (kHoist) {
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
+        for (int i = 0; i < 4; i++) {
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const uint32_t v = __shfl_sync(kFull, tcnt[i], j * 8);
-            if (lane == (uint32_t)(4 * i + j)) tcl = v;
+            for (int j = 0; j < 4; j++) {
+                const uint32_t v = __shfl_sync(kFull, tcnt[i], j * 8);
+                if (lane == (uint32_t)(4 * i + j)) tcl = v;
+            }
         }
     }
     for (int tt = 0; tt < kChunkTiles; tt++) {
-        const uint32_t tc = __shfl_sync(kFull, tcl, tt);
+        uint32_t tc;
+        if constexpr (kHoist) tc = __shfl_sync(kFull, tcl, tt);
+        else tc = __shfl_sync(kFull, tcnt[tt >> 2], (tt & 3) * 8);
         const uint64_t t = (uint64_t)c * kChunkTiles + tt;
         if (tc && t < a.n_tiles && base < a.out_cap) {
             const uint64_t w = t * kTileWords + lane;
