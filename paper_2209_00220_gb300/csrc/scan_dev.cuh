@@ -219,6 +219,27 @@ __device__ __forceinline__ void vbs_deeper(const ScanK &a, uint32_t t, uint32_t 
             const uint32_t c1 = lit_byte(a.lit[0], j);
             const uint32_t c2 = NLIT == 2 ? lit_byte(a.lit[1], j) : 0u;
             uint32_t bits = need;
+            if (NLIT == 1) {
+                // one literal: every pending row is in EQ1; collect "less" and
+                // "differs" over the lane's pending rows, then apply once (the
+                // lane's BS_j bytes are the run [base, base + cnt))
+                if (base + cnt <= dlen) {
+                    const uint8_t *run = deep + base;
+                    uint32_t lt = 0u, ne = 0u;
+                    while (bits) {
+                        const uint32_t bit = bits & (0u - bits);
+                        bits ^= bit;
+                        const uint32_t byte = __ldg(run + __popc(mj & (bit - 1u)));
+                        lt |= byte < c1 ? bit : 0u;
+                        ne |= byte != c1 ? bit : 0u;
+                    }
+                    LT1 |= lt;
+                    EQ1 &= ~ne;
+                } else {
+                    atomicOr(a.status, kStatusBounds);
+                    bits = 0u;
+                }
+            }
             while (bits) {
                 const uint32_t r = __ffs(bits) - 1;
                 const uint32_t bit = 1u << r;
