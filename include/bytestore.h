@@ -75,7 +75,11 @@ typedef struct bs_column bs_column; /* opaque; owns its device buffers */
  *   host_only: 1 = build the layout in host memory only (no GPU needed); such a
  *       column answers bs_column_row_codes / bs_column_get_info but not scans.
  *   keep_host: 1 = keep the host copy of the layout after the upload.
- *   threads: host encoder threads, 0 = every available core. */
+ *   threads: host encoder threads, 0 = every available core.
+ *   categorical: for BS_PPVBS, 1 = codes by Algorithm 2 (categorical columns:
+ *       most frequent values first, ties by smaller value; a balanced tree
+ *       whose codes do not follow value order). Such a column answers only
+ *       = and != (other predicates: UNSUPPORTED); lookups are unchanged. */
 typedef struct {
     int32_t domain_bits;
     int32_t device;
@@ -85,7 +89,7 @@ typedef struct {
     int32_t host_only;
     int32_t keep_host;
     int32_t threads;
-    int32_t reserved;
+    int32_t categorical;
     const uint64_t *domain_counts;
 } bs_encode_opts;
 
@@ -274,12 +278,21 @@ typedef struct {
     double cost_ppvbs[100];
 } bs_advice;
 
-/* Column-layout advisor (Algorithm 5) for one numerical column: encode it as
- * ByteSlice and as PP-VBS, profile `<` scans with 100 literals spread over the
+/* Column-layout advisor (Algorithm 5) for one column: encode it as ByteSlice
+ * and as PP-VBS, profile `<` scans (numerical column) or `=` scans
+ * (opts->categorical: PP-VBS by Algorithm 2) with 100 literals spread over the
  * selectivity range, integrate each profile by the trapezoid rule and keep the
  * smaller area (ties -> ByteSlice). opts as for bs_encode_column. */
 int bs_advise_layout(const int32_t *h_values, uint64_t n, int32_t mode, const bs_encode_opts *opts,
                      bs_advice *out);
+
+/* bs_advise_layout for predicates whose selectivity is known to lie in
+ * [sel_lo, sel_hi] (0 <= sel_lo <= sel_hi <= 1; Section 5 notes the advisor
+ * can take a known range into account): the 100 profiling literals are spread
+ * over that range only. bs_advise_layout is the range [0, 1]. Errors as for
+ * bs_advise_layout, INVALID_ARG for a bad range. */
+int bs_advise_layout_range(const int32_t *h_values, uint64_t n, int32_t mode, const bs_encode_opts *opts,
+                           double sel_lo, double sel_hi, bs_advice *out);
 
 /* ------------------------------------------------------- batched form */
 

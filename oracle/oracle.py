@@ -109,6 +109,14 @@ def ppe_categorical(nd: int) -> tuple[np.ndarray, np.ndarray]:
     return C[:nd].copy(), L[:nd].copy()
 
 
+def frequency_order(A, Q) -> np.ndarray:
+    """Dictionary positions by descending count, equal counts by smaller value
+    (Algorithm 2's input order; the reading of its unstated tie rule)."""
+    A = np.asarray(A)
+    Q = np.asarray(Q, dtype=np.int64)
+    return np.lexsort((A, -Q))
+
+
 def pad(codes, lens, K: int) -> np.ndarray:
     """Zero-pad each code to K bytes (the comparison of Section 3.1.1)."""
     codes = _c(codes, np.uint64)
@@ -236,19 +244,29 @@ def byteslice_block_bytes(rows: int, K: int) -> int:
 class OracleColumn:
     """One column encoded the paper's way, decoded row by row for every query.
 
-    layout: "ppvbs" (Algorithm 1 over the observed dictionary), "byteslice" or
-    "bitpacked" (code = rank in ``domain`` if given, else in the observed
-    dictionary; or code = value - domain_min over a declared 2^domain_bits range).
+    layout: "ppvbs" (Algorithm 1 over the observed dictionary, or Algorithm 2
+    with ``categorical=True``), "byteslice" or "bitpacked" (code = rank in
+    ``domain`` if given, else in the observed dictionary; or code = value -
+    domain_min over a declared 2^domain_bits range).
     """
 
     def __init__(self, values, layout: str, domain=None, domain_bits: int | None = None,
-                 domain_min: int = 0):
+                 domain_min: int = 0, categorical: bool = False):
         self.values = _c(values, np.int32)
         self.n = self.values.size
         self.layout = layout
         if layout == "ppvbs":
             A, Q = dictionary(self.values)
-            C, L = ppe_numerical(Q)
+            if categorical:
+                # Algorithm 2 takes the values in descending frequency (ties:
+                # smaller value first) and hands out its codes in that order
+                rank = frequency_order(A, Q)
+                Cr, Lr = ppe_categorical(A.size)
+                C = np.zeros(A.size, np.uint64)
+                L = np.zeros(A.size, np.uint8)
+                C[rank], L[rank] = Cr, Lr
+            else:
+                C, L = ppe_numerical(Q)
             self.A, self.Q, self.C, self.L = A, Q, C, L
             self.K = int(L.max()) if L.size else 1
             idx = np.searchsorted(A, self.values)

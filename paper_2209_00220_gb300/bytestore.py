@@ -30,7 +30,7 @@ _u64, _i32, _i64, _vp = ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, ctypes.
 class bs_encode_opts(ctypes.Structure):
     _fields_ = [("domain_bits", _i32), ("device", _i32), ("domain_min", _i64), ("domain_values", _vp),
                 ("n_domain", _u64), ("host_only", _i32), ("keep_host", _i32), ("threads", _i32),
-                ("reserved", _i32), ("domain_counts", _vp)]
+                ("categorical", _i32), ("domain_counts", _vp)]
 
 
 class bs_column_info(ctypes.Structure):
@@ -107,6 +107,7 @@ _SIGS = {
     "bs_lookup_noalloc": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
     "bs_lookup_rowids": ([_vp, _vp, _u64, _vp, _vp], _i32),
     "bs_advise_layout": ([_vp, _u64, _i32, _vp, _vp], _i32),
+    "bs_advise_layout_range": ([_vp, _u64, _i32, _vp, ctypes.c_double, ctypes.c_double, _vp], _i32),
     "bs_scan_bytes": ([_vp, _i32, _i32, _i32, _vp, _vp], _i32),
     "bs_lookup_bytes": ([_vp, _vp, _vp], _i32),
     "bs_batch_create": ([_vp, _i32, _vp, _vp], _i32),
@@ -183,8 +184,9 @@ def _np(a, dtype):
 
 
 def _opts(domain_bits=0, domain_min=0, domain_values=None, device=-1, host_only=False, keep_host=False,
-          threads=0, domain_counts=None):
+          threads=0, domain_counts=None, categorical=False):
     o = bs_encode_opts()
+    o.categorical = 1 if categorical else 0
     o.domain_bits = int(domain_bits)
     o.domain_min = int(domain_min)
     o.device = int(device)
@@ -570,12 +572,14 @@ def bs_server_create(max_batch: int = 0, slots: int = 0, result_bytes: int = 0, 
 
 
 # ----------------------------------------------------------------- advisor
-def bs_advise_layout(values, mode: int = ADVISE_BYTES_MODEL, **opts) -> dict:
+def bs_advise_layout(values, mode: int = ADVISE_BYTES_MODEL, sel_range=None, **opts) -> dict:
+    """sel_range: optional (lo, hi) selectivity range the predicates are known to fall in."""
     v = _np(values, np.int32)
     o, keep = _opts(**opts)
     a = bs_advice()
-    _check(lib().bs_advise_layout(v.ctypes.data if v.size else None, v.size, int(mode), ctypes.byref(o),
-                                  ctypes.byref(a)), "bs_advise_layout")
+    lo, hi = (0.0, 1.0) if sel_range is None else (float(sel_range[0]), float(sel_range[1]))
+    _check(lib().bs_advise_layout_range(v.ctypes.data if v.size else None, v.size, int(mode), ctypes.byref(o),
+                                        lo, hi, ctypes.byref(a)), "bs_advise_layout_range")
     k = a.n_points
     return {"layout": {0: "bitpacked", 1: "byteslice", 2: "ppvbs"}[a.layout], "auc_byteslice": a.auc_byteslice,
             "auc_ppvbs": a.auc_ppvbs, "selectivity": list(a.selectivity[:k]),

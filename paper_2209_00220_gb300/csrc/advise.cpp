@@ -1,13 +1,15 @@
 // Column-layout advisor (Algorithm 5) and the C entry points of the
 // effective-bytes counter.
 //
-// For one numerical column: encode it as ByteSlice (dictionary codes) and as
-// PP-VBS (Algorithm 1), pick 100 literals from the column whose `<`
-// selectivities span the feasible range (the value at row quantile (i+0.5)/100,
-// rounded up to the smallest value reaching it), measure each scan on both
-// layouts, integrate each (selectivity, cost) profile with the trapezoid rule
-// and keep the layout with the smaller area; ties go to ByteSlice, as the
-// algorithm's "Y <= Z" test does.
+// For one column: encode it as ByteSlice (dictionary codes) and as PP-VBS
+// (Algorithm 1, or Algorithm 2 for a categorical column), pick 100 literals
+// from the column whose selectivities span the feasible range -- numerical:
+// `<` with the value at row quantile (i+0.5)/100, rounded up to the smallest
+// value reaching it; categorical: `=` with the values at evenly spaced
+// frequency ranks -- measure each scan on both layouts, integrate each
+// (selectivity, cost) profile with the trapezoid rule and keep the layout with
+// the smaller area; ties go to ByteSlice, as the algorithm's "Y <= Z" test
+// does.
 //   TIMED:       cost = median of 3 CUDA-event timings of bs_scan on the device.
 //   BYTES_MODEL: cost = bytes the scan must move (effective-bytes counter), a
 //                deterministic stand-in that needs no GPU.
@@ -55,10 +57,11 @@ int bs_lookup_bytes(const bs_column *col, const uint32_t *h_bits, bs_lookup_byte
     return bs::lookup_bytes(col->c, h_bits, out);
 }
 
-int bs_advise_layout(const int32_t *h_values, uint64_t n, int32_t mode, const bs_encode_opts *opts,
-                     bs_advice *out) {
+int bs_advise_layout_range(const int32_t *h_values, uint64_t n, int32_t mode, const bs_encode_opts *opts,
+                           double sel_lo, double sel_hi, bs_advice *out) {
     if (!out || (n && !h_values) || (mode != BS_ADVISE_TIMED && mode != BS_ADVISE_BYTES_MODEL))
         return BS_ERR_INVALID_ARG;
+    if (!(sel_lo >= 0.0 && sel_lo <= sel_hi && sel_hi <= 1.0)) return BS_ERR_INVALID_ARG;
     std::memset(out, 0, sizeof *out);
     bs_encode_opts o;
     std::memset(&o, 0, sizeof o);
@@ -82,21 +85,44 @@ int bs_advise_layout(const int32_t *h_values, uint64_t n, int32_t mode, const bs
         bs_column_free(bsl);
         return rc;
     }
-    // literals: row quantiles of the value distribution (PP-VBS dictionary counts)
     const Column &cv = vbs->c;
     const std::vector<uint64_t> &Q = cv.dcount;
-    std::vector<uint64_t> cum(Q.size() + 1, 0);
-    for (size_t i = 0; i < Q.size(); i++) cum[i + 1] = cum[i] + Q[i];
     const int P = 100;
     std::vector<int32_t> lits(P);
     std::vector<double> sel(P);
-    for (int i = 0; i < P; i++) {
-        const double target = ((double)i + 0.5) / P * (double)n;
-        size_t u = 0;
-        while (u + 1 < cum.size() && (double)cum[u] < target) u++;
-        if (u >= cv.dict.size()) u = cv.dict.empty() ? 0 : cv.dict.size() - 1;
-        lits[i] = cv.dict.empty() ? 0 : cv.dict[u];
-        sel[i] = n ? (double)cum[u] / (double)n : 0.0;
+    const bs_op op = o.categorical ? BS_EQ : BS_LT;
+    if (o.categorical) {
+        // categorical: `=` with values at evenly spaced frequency ranks among
+        // those whose selectivity lies in [sel_lo, sel_hi] (the nearest rank
+        // when none does; the whole range: from the most frequent value down)
+        std::vector<uint32_t> order(Q.size());
+        for (size_t i = 0; i < Q.size(); i++) order[i] = (uint32_t)i;
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return Q[x] > Q[y]; });
+        size_t r0 = 0, r1 = order.empty() ? 0 : order.size() - 1;
+        if (!order.empty() && n) {
+            auto s_of = [&](size_t r) { return (double)Q[order[r]] / (double)n; };
+            while (r0 < r1 && s_of(r0) > sel_hi) r0++;   // counts fall along the ranks
+            while (r1 > r0 && s_of(r1) < sel_lo) r1--;
+        }
+        for (int i = 0; i < P; i++) {
+            const size_t r = order.empty() ? 0 : r0 + (size_t)((double)i * (double)(r1 - r0) / (P - 1) + 0.5);
+            const size_t u = order.empty() ? 0 : order[r];
+            lits[i] = cv.dict.empty() ? 0 : cv.dict[u];
+            sel[i] = n && !Q.empty() ? (double)Q[u] / (double)n : 0.0;
+        }
+    } else {
+        // numerical: `<` with literals at row quantiles sel_lo + (i + 0.5) / 100
+        // * (sel_hi - sel_lo) (the whole range: (i + 0.5) / 100)
+        std::vector<uint64_t> cum(Q.size() + 1, 0);
+        for (size_t i = 0; i < Q.size(); i++) cum[i + 1] = cum[i] + Q[i];
+        for (int i = 0; i < P; i++) {
+            const double target = (sel_lo + ((double)i + 0.5) / P * (sel_hi - sel_lo)) * (double)n;
+            size_t u = 0;
+            while (u + 1 < cum.size() && (double)cum[u] < target) u++;
+            if (u >= cv.dict.size()) u = cv.dict.empty() ? 0 : cv.dict.size() - 1;
+            lits[i] = cv.dict.empty() ? 0 : cv.dict[u];
+            sel[i] = n ? (double)cum[u] / (double)n : 0.0;
+        }
     }
     std::vector<double> cost_b(P, 0.0), cost_v(P, 0.0);
     if (mode == BS_ADVISE_BYTES_MODEL) {
@@ -104,8 +130,8 @@ int bs_advise_layout(const int32_t *h_values, uint64_t n, int32_t mode, const bs
         for (int i = 0; i < P && rc == BS_OK; i++) {
             bs::KPred pb, pv;
             bs_scan_bytes_t sb, sv;
-            rc = bs::rewrite_literal(bsl->c, BS_LT, lits[i], 0, pb);
-            if (!rc) rc = bs::rewrite_literal(vbs->c, BS_LT, lits[i], 0, pv);
+            rc = bs::rewrite_literal(bsl->c, op, lits[i], 0, pb);
+            if (!rc) rc = bs::rewrite_literal(vbs->c, op, lits[i], 0, pv);
             if (!rc) rc = bs::scan_bytes(bsl->c, pb, nullptr, stride, &sb);
             if (!rc) rc = bs::scan_bytes(vbs->c, pv, nullptr, stride, &sv);
             cost_b[i] = (double)sb.bytes;
@@ -119,10 +145,10 @@ int bs_advise_layout(const int32_t *h_values, uint64_t n, int32_t mode, const bs
         if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = BS_ERR_CUDA;
         auto time_scan = [&](const bs_column *c, int32_t lit, double &secs) -> int {
             float ms[3];
-            int r = bs_scan(c, BS_LT, lit, 0, d_bits, nullptr);  // warm-up
+            int r = bs_scan(c, op, lit, 0, d_bits, nullptr);  // warm-up
             for (int k = 0; k < 3 && !r; k++) {
                 cudaEventRecord(e0, nullptr);
-                r = bs_scan(c, BS_LT, lit, 0, d_bits, nullptr);
+                r = bs_scan(c, op, lit, 0, d_bits, nullptr);
                 cudaEventRecord(e1, nullptr);
                 if (cudaEventSynchronize(e1) != cudaSuccess) r = BS_ERR_CUDA;
                 cudaEventElapsedTime(&ms[k], e0, e1);
@@ -155,6 +181,11 @@ int bs_advise_layout(const int32_t *h_values, uint64_t n, int32_t mode, const bs
     out->auc_ppvbs = trapezoid(pv);
     out->layout = out->auc_byteslice <= out->auc_ppvbs ? BS_BYTESLICE : BS_PPVBS;
     return BS_OK;
+}
+
+int bs_advise_layout(const int32_t *h_values, uint64_t n, int32_t mode, const bs_encode_opts *opts,
+                     bs_advice *out) {
+    return bs_advise_layout_range(h_values, n, mode, opts, 0.0, 1.0, out);
 }
 
 }  // extern "C"

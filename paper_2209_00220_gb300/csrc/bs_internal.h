@@ -71,6 +71,9 @@ struct Column {
     int k = 0;                  // ByteSlice / Bit-Packed code bits
     int S = 0;                  // ByteSlice slices
     int K = 1;                  // PP-VBS longest code in bytes
+    bool categorical = false;   // PP-VBS codes by Algorithm 2 (= and != only)
+    int cat_B = 0;              // Algorithm 2: levels of the balanced tree
+    std::vector<int32_t> rank_dict;  // Algorithm 2: values in code-assignment (frequency) order
     std::vector<int32_t> dict;  // sorted distinct values (dictionary)
     std::vector<uint64_t> dcode;  // PP-VBS: code of dict[i] (unpadded)
     std::vector<uint8_t> dlen;    // PP-VBS: its length in bytes

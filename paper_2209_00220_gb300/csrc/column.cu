@@ -148,7 +148,11 @@ int upload_column(Column &c) {
         ok = ok && put(o_packed, c.h_packed.data(), c.h_packed.size() * 4);
         c.d_packed = (const uint32_t *)(b + o_packed);
     }
-    ok = ok && put(o_dict, c.dict.data(), c.dict.size() * 4);
+    // the device dictionary is indexed by what a code decodes to: the value
+    // position for Algorithm 1 and the fixed-width layouts, the frequency rank
+    // for Algorithm 2
+    const std::vector<int32_t> &ddict = c.categorical ? c.rank_dict : c.dict;
+    ok = ok && put(o_dict, ddict.data(), ddict.size() * 4);
     c.d_dict = (const int32_t *)(b + o_dict);
     c.d_arena = base;
     c.d_bytes = total;

@@ -281,6 +281,58 @@ static void ppe_numerical(const std::vector<uint64_t> &Q, std::vector<uint64_t> 
 // whose values have consecutive dictionary indices and codes 1, 2, ... after
 // the two-byte pointer path -- leaf2 holds the dictionary index of the leaf's
 // first value, so value = dict[leaf2[c1 c2] + rest - 1].
+// ---------------------------------------------------------- Algorithm 2
+// The balanced tree of the categorical encoding, in closed form: levels
+// 1..B-1 are full (level b holds 255 * 256^(b-1) codes: pointer path p, slot
+// i = 1..255, code p * 256 + i, in that order); the last level B takes the
+// remaining values slot-major (slot i outermost, then pointer path j), which
+// spreads them evenly over the last-level nodes. B = ceil(log_256(nd + 1)).
+static int categorical_levels(uint64_t nd) {
+    int B = 1;
+    uint64_t cap = 256;  // 256^B
+    while (cap < nd + 1) {
+        cap <<= 8;
+        B++;
+    }
+    return B;
+}
+
+// code and length of the value with frequency rank r (0 = most frequent)
+static void categorical_code(uint64_t r, int B, uint64_t &code, uint8_t &len) {
+    uint64_t before = 0, level = 255;  // codes on the levels above, codes on this level
+    for (int b = 1; b < B; b++) {
+        if (r < before + level) {
+            const uint64_t q = r - before;
+            code = (q / 255) * 256 + (q % 255) + 1;
+            len = (uint8_t)b;
+            return;
+        }
+        before += level;
+        level <<= 8;
+    }
+    const uint64_t q = r - before, paths = 1ull << (8 * (B - 1));  // 256^(B-1) last-level nodes
+    code = (q % paths) * 256 + (q / paths) + 1;
+    len = (uint8_t)B;
+}
+
+static void ppe_categorical(const std::vector<int32_t> &A, const std::vector<uint64_t> &Q, Column &c) {
+    const uint64_t nd = A.size();
+    std::vector<uint32_t> order(nd);
+    for (uint64_t i = 0; i < nd; i++) order[i] = (uint32_t)i;
+    // descending frequency; A is sorted, so a stable sort keeps ties by smaller value
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return Q[x] > Q[y]; });
+    const int B = nd ? categorical_levels(nd) : 1;
+    c.dcode.assign(nd, 0);
+    c.dlen.assign(nd, 1);
+    c.rank_dict.assign(nd, 0);
+    for (uint64_t r = 0; r < nd; r++) {
+        categorical_code(r, B, c.dcode[order[r]], c.dlen[order[r]]);
+        c.rank_dict[r] = A[order[r]];
+    }
+    c.categorical = true;
+    c.cat_B = B;
+}
+
 static void build_decode_tables(Column &c) {
     c.val2.assign(65536, 0);
     c.leaf2.assign(65536, 0);
@@ -293,7 +345,7 @@ static void build_decode_tables(Column &c) {
             c.val1[(size_t)C] = c.dict[i];
         } else if (L == 2) {
             c.val2[(size_t)C] = c.dict[i];
-        } else {
+        } else if (!c.categorical) {  // Algorithm 2's longer codes decode by arithmetic instead
             const uint64_t key = C >> (8 * (L - 2));
             const uint64_t rest = C & ((1ull << (8 * (L - 2))) - 1);
             c.leaf2[(size_t)key] = (uint32_t)(i - (rest - 1));
@@ -485,13 +537,13 @@ int encode_values(const int32_t *values, uint64_t n, bs_layout layout, const bs_
                 // larger column); Q below is then recounted over this column's rows
                 int rc = declared_dictionary(values, n, T, o, c.dict, Q, ridx);
                 if (rc) return rc;
-                ppe_numerical(Q, c.dcode, c.dlen, T);
-                count_rows(ridx, c.dict.size(), T, Q);
             } else {
                 int rc = build_dictionary(values, n, T, c.dict, Q, ridx);
                 if (rc) return rc;
-                ppe_numerical(Q, c.dcode, c.dlen, T);
             }
+            if (o.categorical) ppe_categorical(c.dict, Q, c);
+            else ppe_numerical(Q, c.dcode, c.dlen, T);
+            if (o.domain_counts) count_rows(ridx, c.dict.size(), T, Q);
             c.dcount = Q;
             c.dcum.assign(Q.size() + 1, 0);
             for (size_t i = 0; i < Q.size(); i++) c.dcum[i + 1] = c.dcum[i] + Q[i];
@@ -648,6 +700,8 @@ int rewrite_literal(const Column &c, int op, int32_t lit, int32_t lit2, KPred &o
     out = KPred{};
     out.mode = Pred::kNormal;
     if (c.raw) return BS_ERR_UNSUPPORTED;
+    // Algorithm 2's codes do not follow value order: equality predicates only
+    if (c.categorical && op != BS_EQ && op != BS_NE) return BS_ERR_UNSUPPORTED;
     CodeSpace cs{c};
     const uint64_t N = cs.size();
     auto set = [&](int kop, uint64_t u) { out.op = kop; out.lit[0] = cs.code(u); };

@@ -53,6 +53,8 @@ constexpr uint32_t kSparseMax = 256;  // selected rows up to which a chunk is re
 struct LookK {
     int32_t layout;
     int32_t K;            // PP-VBS longest code / ByteSlice slices
+    int32_t categorical;  // PP-VBS codes by Algorithm 2 (dict in frequency-rank order)
+    int32_t cat_B;        // Algorithm 2: levels of the tree
     int32_t k;            // code bits (ByteSlice / Bit-Packed)
     int32_t identity;
     int64_t domain_min;
@@ -138,6 +140,20 @@ __device__ __forceinline__ int32_t decode_value(const LookK &a, uint64_t code, i
         const uint32_t c2 = len >= 2 ? (uint32_t)(code >> (8 * (len - 2))) & 0xFFu : 0u;
         const uint32_t key = (c1 << 8) | c2;
         if (len <= 2) return __ldg(a.val2 + key);
+        if (a.categorical) {
+            // Algorithm 2: the rank follows from the code's level and position
+            // (levels above the last: pointer path * 255 + slot - 1; the last
+            // level: (slot - 1) * 256^(B-1) + pointer path)
+            uint64_t before = 0, level = 255;
+            for (int b = 1; b < len; b++) {
+                before += level;
+                level <<= 8;
+            }
+            const uint64_t slot = code & 0xFFu, path = code >> 8;
+            const uint64_t rank =
+                len < a.cat_B ? before + path * 255 + (slot - 1) : before + (slot - 1) * (1ull << (8 * (len - 1))) + path;
+            return dict_value(a, rank);
+        }
         const uint64_t rest = code & ((1ull << (8 * (len - 2))) - 1);
         return dict_value(a, (uint64_t)__ldg(a.leaf2 + key) + rest - 1);
     }
@@ -612,6 +628,8 @@ inline LookK make_look_args(const Column &c) {
     LookK a{};
     a.layout = c.layout;
     a.K = c.layout == BS_PPVBS ? c.K : c.S;
+    a.categorical = c.categorical ? 1 : 0;
+    a.cat_B = c.cat_B;
     a.k = c.k;
     a.identity = c.identity ? 1 : 0;
     a.domain_min = c.domain_min;

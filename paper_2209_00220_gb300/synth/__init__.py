@@ -186,6 +186,17 @@ def lognormal_amounts(n: int, mu: float, sigma: float, cap_bits: int, seed: int)
     return np.minimum(a, float((1 << cap_bits) - 1)).astype(np.int32)
 
 
+def gaussian_column(n: int, d: int, sigma: float, seed: int) -> np.ndarray:
+    """Values in [0, 2^d): round(2^(d-1) + sigma * 2^d * z) clipped, z standard
+    normal (the Gaussian data of Section 6's extra experiments; sigma is the
+    standard deviation as a fraction of the domain)."""
+    u1 = _uniform01(seed, 41, n)
+    u2 = _uniform01(seed, 42, n)
+    z = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+    x = np.rint(float(1 << (d - 1)) + sigma * float(1 << d) * z)
+    return np.clip(x, 0, (1 << d) - 1).astype(np.int64).astype(np.int32)
+
+
 # (name, kind, parameters) of the 20 columns of the synthetic denormalised wide
 # table: 5 categorical, 4 date-like day counts, 1 monotone id, 4 heavy-tailed
 # amounts, 6 mixed uniform / Zipf columns.

@@ -131,3 +131,32 @@ def test_timed_mode_on_gpu(B):
     assert min(t["cost_byteslice"]) > 0 and min(t["cost_ppvbs"]) > 0
     assert t["auc_ppvbs"] == pytest.approx(_trapezoid(t["selectivity"], t["cost_ppvbs"]), rel=1e-12)
     assert B.bs_last_device_error() == 0
+
+
+def test_categorical_profile_uses_equality_at_frequency_ranks(B):
+    v = synth.config_sweep_column(1 << 18, 12, 1.2, 5)
+    a = _advise(B, v, categorical=True)
+    vals, counts = np.unique(v, return_counts=True)
+    order = np.lexsort((vals, -counts))
+    ranks = [int(i * (order.size - 1) / 99 + 0.5) for i in range(100)]
+    assert np.allclose(a["selectivity"], counts[order[ranks]] / v.size, rtol=0, atol=0)
+    assert a["auc_byteslice"] == pytest.approx(_trapezoid(np.array(a["selectivity"]), a["cost_byteslice"]), rel=1e-12)
+
+
+def test_known_selectivity_range_restricts_the_profile(B):
+    # Section 5: with a known selectivity range the advisor profiles only it
+    v = synth.config_sweep_column(1 << 18, 12, 1.0, 8)
+    a = _advise(B, v, sel_range=(0.2, 0.4))
+    sel = np.array(a["selectivity"])
+    vals, counts = np.unique(v, return_counts=True)
+    cum = np.concatenate([[0], np.cumsum(counts)])
+    want = []
+    for i in range(100):
+        u = min(int(np.searchsorted(cum, (0.2 + (i + 0.5) / 100 * 0.2) * v.size, side="left")), vals.size - 1)
+        want.append(cum[u] / v.size)
+    assert np.array_equal(sel, np.array(want))
+    assert sel.min() >= 0.2 - 0.05 and sel.max() <= 0.4 + 0.05
+    c = _advise(B, v, categorical=True, sel_range=(0.0, 0.01))
+    assert max(c["selectivity"]) <= 0.01
+    with pytest.raises(B.BsError):
+        _advise(B, v, sel_range=(0.5, 0.2))

@@ -109,6 +109,9 @@ def _value_cases():
         "bitpacked": {"domain_bits": 32, "domain_min": -(1 << 31)}}
     yield "d8_declared", synth.config_sweep_column(33000, 8, 1.0, 17), {
         "byteslice": {"domain_bits": 8}, "bitpacked": {"domain_bits": 8}}
+    # Gaussian data (Section 6's additional experiments): narrow and wide
+    yield "gauss_d16_narrow", synth.gaussian_column(120000, 16, 0.01, 18), {}
+    yield "gauss_d20_wide", synth.gaussian_column(90000, 20, 0.2, 19), {}
 
 
 def _literals(v, seed):

@@ -130,3 +130,24 @@ def test_encoder_rejects_bad_input(B):
         B.bs_encode_column(v, "byteslice", host_only=True, domain_bits=4)  # values outside 0..15
     with pytest.raises(B.BsError):
         B.bs_column_from_codes(np.array([0x1FF], np.uint64), np.array([1], np.uint8), "ppvbs", host_only=True)
+
+
+@pytest.mark.parametrize("n,d,s,seed", [(50000, 8, 1.0, 1), (120000, 12, 0.7, 2), (300000, 17, 0.3, 3),
+                                        (200000, 20, 1.4, 4)])
+def test_categorical_codes_match_oracle(B, n, d, s, seed):
+    v = synth.config_sweep_column(n, d, s, seed)
+    ocol = orc.OracleColumn(v, "ppvbs", categorical=True)
+    col = B.bs_encode_column(v, "ppvbs", categorical=True, host_only=True)
+    codes, lens = B.bs_column_row_codes(col)
+    assert np.array_equal(codes, ocol.row_codes) and np.array_equal(lens, ocol.row_lens)
+    dv, dc, dl = B.bs_column_dictionary(col)
+    assert np.array_equal(dv, ocol.A) and np.array_equal(dc, ocol.C) and np.array_equal(dl, ocol.L)
+
+
+def test_categorical_columns_take_only_equality(B):
+    v = synth.config_sweep_column(5000, 10, 1.0, 9)
+    col = B.bs_encode_column(v, "ppvbs", categorical=True, host_only=True)
+    for op in ("lt", "le", "gt", "ge", "between"):
+        with pytest.raises(B.BsError):
+            B.bs_scan_bytes(col, op, int(v[0]), int(v[0]))
+    assert B.bs_scan_bytes(col, "eq", int(v[0]))["bytes"] > 0

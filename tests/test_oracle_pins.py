@@ -371,3 +371,28 @@ def test_code_scan_equals_value_scan_under_order_preservation():
         for op in ("lt", "le", "gt", "ge", "eq", "ne"):
             assert np.array_equal(orc.scan_codes(padded, op, int(dict_pad[t])),
                                   orc.scan_values(v, op, int(col.A[t])))
+
+
+# ------------------------------------------ Algorithm 2 inside a column
+def test_categorical_column_hands_out_codes_by_frequency():
+    # counts: 3 and 7 five times (tie: the smaller value first), 9 twice, 1 once
+    v = np.array([7] * 5 + [3] * 5 + [9] * 2 + [1], np.int32)
+    oc = orc.OracleColumn(v, "ppvbs", categorical=True)
+    code = {int(a): (int(c), int(l)) for a, c, l in zip(oc.A, oc.C, oc.L)}
+    assert code == {3: (1, 1), 7: (2, 1), 9: (3, 1), 1: (4, 1)}
+    assert np.array_equal(oc.decode_values(), v)
+
+
+def test_categorical_column_second_level_and_roundtrip():
+    # 300 values with distinct counts 300, 299, ..., 1 (value i has count 300 - i)
+    vals = np.repeat(np.arange(300, dtype=np.int32), np.arange(300, 0, -1))
+    oc = orc.OracleColumn(vals, "ppvbs", categorical=True)
+    assert oc.K == 2
+    # ranks 0..254 take the one-byte codes 1..255; rank 255 + j takes (j, 1)
+    assert [int(c) for c in oc.C[:255]] == list(range(1, 256))
+    assert [int(c) for c in oc.C[255:]] == [(j << 8) | 1 for j in range(45)]
+    assert np.array_equal(oc.decode_values(), vals)
+    # three levels once more than 255 + 256 * 255 values exist
+    big = np.arange(70000, dtype=np.int32)
+    ob = orc.OracleColumn(big, "ppvbs", categorical=True)
+    assert ob.K == 3 and np.array_equal(ob.decode_values(), big)
