@@ -15,7 +15,7 @@ namespace {
 // PF: the tile's M_2 words travel in the ring with its BS_1 bytes (chosen on
 // the host when most tiles are expected to hold rows pending after byte 1).
 template <bool VBS, int NLIT, bool HI0, bool HI1, bool NEED_EQ, bool PF>
-__global__ void __launch_bounds__(kScanThreads) scan_dense_kernel(const ScanK a) {
+__global__ void __launch_bounds__(kScanThreads, 8) scan_dense_kernel(const ScanK a) {
     constexpr int kSlot = kTileRows + (PF ? kTileWords * 4 : 0);
     static_assert(kSlot % 16 == 0, "ring slots receive 16-byte cp.async copies");
     __shared__ __align__(16) uint8_t ring[kScanWarps][kStages][kSlot];
