@@ -41,6 +41,8 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# side files (clock samples, the batch shape cache): BENCH_OUT_DIR, else the temp dir
+OUT_DIR = os.environ.get("BENCH_OUT_DIR") or __import__("tempfile").gettempdir()
 
 METRIC = "scan Grows/s & % of HBM roofline; lookup Gvals/s; batched p50/p99 latency"
 
@@ -87,7 +89,7 @@ class Clocks:
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu)
+        self.path = os.path.join(OUT_DIR, "clocks_rank%d.csv" % gpu)
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -229,7 +231,7 @@ def run_batched(B, warmup=2, steps=5, seed=0):
 
     reqs = [{"preds": [(cols[ci], op, a, b)], "out": outs_batch[i], "out_cap": int(counts[i]),
              "count": cnt_b[i:i + 1]} for i, (ci, op, a, b) in enumerate(spec)]
-    cache = os.path.join(ROOT, "gpurun_out", "batch_tune.jsonl")
+    cache = os.path.join(OUT_DIR, "batch_tune.jsonl")
     os.makedirs(os.path.dirname(cache), exist_ok=True)
     batch = B.bs_batch_create(reqs, autotune=True, tune_cache=cache)
     for _ in range(warmup):
