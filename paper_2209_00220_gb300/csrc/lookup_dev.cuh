@@ -446,22 +446,23 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
     uint4 *rows = reinterpret_cast<uint4 *>(sm.dense + lane * 32u);
     rows[0] = r0;
     rows[1] = r1;
-    __syncwarp();
-    const uint8_t *seg = reinterpret_cast<const uint8_t *>(sm.seg) + (seg_lo & 3u);
-    const uint32_t p2 = goff + inc2 - c2 - seg_lo;  // lane's first BS_2 byte, relative to the segment
-    // each selected row: its BS_1 byte and the BS_2 byte at its rank among the
-    // lane's two-byte rows, read unconditionally (the rank stays inside the
-    // staged segment) and kept only for rows whose M_2 bit is set
+    // per lane word: its M_2 bits and its first BS_2 byte, relative to the
+    // staged segment
+    sm.mask[2][lane] = m2;
+    sm.pref[2][lane] = goff + inc2 - c2 - seg_lo;
+    // the lane's selected rows, in row order, at its output positions
     uint32_t pos = incl - cnt, r = sel;
     while (r) {
         const uint32_t b = __ffs(r) - 1;
         r &= r - 1;
-        const uint32_t c1 = sm.dense[lane * 32u + b];
-        const uint32_t c2b = seg[p2 + __popc(m2 & ((1u << b) - 1u))];
-        sm.list[pos++] = (uint16_t)((c1 << 8) | (((m2 >> b) & 1u) ? c2b : 0u));
+        sm.list[pos++] = (uint16_t)(lane * 32u + b);
     }
     __syncwarp();
-    // decode and store, 32-bit indexes inside the tile's output range
+    // every output slot by the lanes in turn: its row's first byte, the BS_2
+    // byte at the row's rank among its word's two-byte rows (read
+    // unconditionally: the rank stays inside the staged segment; kept only if
+    // the row's M_2 bit is set), then the value of the two-byte key
+    const uint8_t *seg = reinterpret_cast<const uint8_t *>(sm.seg) + (seg_lo & 3u);
     const uint64_t room = a.out_cap > out_base ? a.out_cap - out_base : 0;
     const uint32_t lim = (uint32_t)(room < total ? room : total);
     int32_t *dst = a.out_vals + out_base;
@@ -472,8 +473,12 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
             const uint32_t i = i0 + (uint32_t)u * 32u + lane;
             v[u] = 0;
             if (i < lim) {
-                const uint32_t key = sm.list[i];
-                v[u] = (key & 0xFFu) ? __ldg(a.val2 + key) : val1[key >> 8];
+                const uint32_t q = sm.list[i], w = q >> 5, b = q & 31u;
+                const uint32_t mw = sm.mask[2][w];
+                const uint32_t c1 = sm.dense[q];
+                const uint32_t c2b = seg[sm.pref[2][w] + __popc(mw & ((1u << b) - 1u))];
+                const uint32_t key = (c1 << 8) | (((mw >> b) & 1u) ? c2b : 0u);
+                v[u] = (key & 0xFFu) ? __ldg(a.val2 + key) : val1[c1];
             }
         }
 #pragma unroll
@@ -614,6 +619,19 @@ __device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_
                 const uint32_t e = (uint32_t)tt * kGroupsPerTile;
                 const uint32_t goff = off_entry(e + (lane >> 3));
                 const uint32_t lo = off_entry(e), hi = off_entry(e + kGroupsPerTile);
+                const uint32_t tc1 = kHoist && tt + 1 < kChunkTiles ? __shfl_sync(kFull, tcl, (tt + 1) & 31) : 0u;
+                if (tc1 >= kStageMin && t + 1 < a.n_tiles) {
+                    // the next tile is dense too: its bytes into L2 while this
+                    // one is resolved -- BS_1 (lanes 0..7), M_2 (lane 8), the
+                    // start of its BS_2 segment (lanes 9..12), a 128-byte line each
+                    const uint32_t nlo = hi;
+                    const uint8_t *pa = nullptr;
+                    if (lane < 8u) pa = a.dense + (t + 1) * kTileRows + lane * 128u;
+                    else if (lane == 8u && a.K >= 2) pa = reinterpret_cast<const uint8_t *>(a.mask[2] + (t + 1) * kTileWords);
+                    else if (lane >= 9u && lane < 13u && a.K >= 2 && (uint64_t)nlo + (lane - 9u) * 128u < a.deep_len[2])
+                        pa = a.deep[2] + (uint64_t)nlo + (lane - 9u) * 128u;
+                    if (pa) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+                }
                 gather_dense_k2(a, t, sel, base, goff, lo, hi, reinterpret_cast<WarpSmemT<2> &>(sm), val1, lane);
             } else {
                 gather_tile<LAYOUT, CODES, KMAX>(a, t, sel, base, sm, val1, lane);
