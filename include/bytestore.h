@@ -104,6 +104,21 @@ typedef struct {
 int bs_encode_column(const int32_t *h_values, uint64_t n, bs_layout layout,
                      const bs_encode_opts *opts, bs_column **out);
 
+/* Write an encoded column to a file (the dictionary side and the layout's byte
+ * arrays; a column without a host copy is read back from the device), so that
+ * a column encoded once can be loaded instead of re-encoded. Errors:
+ * INVALID_ARG (NULL, file not writable), UNSUPPORTED (neither a host nor a
+ * device copy), CUDA. Not part of the paper. */
+int bs_column_save(const bs_column *col, const char *path);
+
+/* Read a column written by bs_column_save and place it like bs_encode_column
+ * would (opts: device, host_only, keep_host; the other fields are ignored).
+ * The file is checked for the magic, for sizes that fit the column's row
+ * count and for the array sizes the kernels rely on. On success *out owns a
+ * new column. Errors: INVALID_ARG (missing, truncated or inconsistent file),
+ * OOM, CUDA. */
+int bs_column_load(const char *path, const bs_encode_opts *opts, bs_column **out);
+
 /* Test hook: build a column straight from codes, without a dictionary.
  * PP-VBS: h_codes[i] is an unpadded code of h_lens[i] bytes (1..8; first byte
  * most significant) -- any code set whose every extension of a shorter code has
@@ -438,6 +453,14 @@ void bs_server_destroy(bs_server *s);
 /* -------------------------------------------------------- diagnostics */
 
 const char *bs_strerror(int status);
+
+/* Test hook (the paper has no counterpart): one device thread waits for a flag
+ * that nothing sets, with the same bounded wait the batched kernel's grid
+ * barrier uses (at most max_polls polls, max_polls <= 2^24). *gave_up = 1 when
+ * the wait gave up as it must; it also leaves a timeout in the device status
+ * word, which the next bs_last_device_error reports as BS_ERR_TIMEOUT. Errors:
+ * INVALID_ARG, OOM, CUDA. */
+int bs_selftest_bounded_wait(uint32_t max_polls, int32_t *gave_up);
 
 /* Reads and clears the device status word of the current device (a kernel
  * bounds check or a bounded wait that gave up). Synchronises the device.

@@ -108,6 +108,9 @@ _SIGS = {
     "bs_lookup_rowids": ([_vp, _vp, _u64, _vp, _vp], _i32),
     "bs_advise_layout": ([_vp, _u64, _i32, _vp, _vp], _i32),
     "bs_advise_layout_range": ([_vp, _u64, _i32, _vp, ctypes.c_double, ctypes.c_double, _vp], _i32),
+    "bs_selftest_bounded_wait": ([ctypes.c_uint32, _vp], _i32),
+    "bs_column_save": ([_vp, ctypes.c_char_p], _i32),
+    "bs_column_load": ([ctypes.c_char_p, _vp, _vp], _i32),
     "bs_scan_bytes": ([_vp, _i32, _i32, _i32, _vp, _vp], _i32),
     "bs_lookup_bytes": ([_vp, _vp, _vp], _i32),
     "bs_batch_create": ([_vp, _i32, _vp, _vp], _i32),
@@ -266,6 +269,20 @@ def bs_column_get_info(col: Column) -> dict:
     return {"n_rows": i.n_rows, "layout": i.layout, "max_code_bytes": i.max_code_bytes,
             "code_bits": i.code_bits, "on_device": bool(i.on_device), "n_dict": i.n_dict,
             "device_bytes": i.device_bytes, "layout_bytes": i.layout_bytes, "len_hist": list(i.len_hist)}
+
+
+def bs_column_save(col: Column, path: str):
+    _check(lib().bs_column_save(col.handle, os.fsencode(path)), "bs_column_save")
+
+
+def bs_column_load(path: str, **opts) -> Column:
+    """opts: device, host_only, keep_host (as for bs_encode_column)."""
+    o, keep = _opts(**opts)
+    out = _vp()
+    _check(lib().bs_column_load(os.fsencode(path), ctypes.byref(o), ctypes.byref(out)), "bs_column_load")
+    col = Column(out.value, 0)
+    col.n = col.info()["n_rows"]
+    return col
 
 
 def bs_column_row_codes(col: Column, begin: int = 0, count: int | None = None):
@@ -452,6 +469,8 @@ def bs_batch_create(requests, threads: int = 0, blocks_per_sm: int = 0, autotune
     keep = []
     for i, q in enumerate(requests):
         preds = q["preds"]
+        if not 1 <= len(preds) <= len(arr[i].preds):
+            raise BsError(BS_ERR_INVALID_ARG, "bs_batch_create: 1..%d predicates per request" % len(arr[i].preds))
         arr[i].npreds = len(preds)
         for j, p in enumerate(preds):
             arr[i].preds[j].col = p[0].handle
@@ -502,6 +521,8 @@ class Server:
     def prepare(preds, proj=None) -> bs_query:
         """The bs_query for (preds, proj), built ahead of submission."""
         q = bs_query()
+        if not 1 <= len(preds) <= len(q.preds):
+            raise BsError(BS_ERR_INVALID_ARG, "bs_server_submit: 1..%d predicates per query" % len(q.preds))
         q.npreds = len(preds)
         for j, p in enumerate(preds):
             q.preds[j].col = p[0].handle
@@ -593,6 +614,13 @@ def bs_strerror(status: int) -> str:
 
 def bs_last_device_error() -> int:
     return int(lib().bs_last_device_error())
+
+
+def bs_selftest_bounded_wait(max_polls: int = 1 << 14) -> bool:
+    """True when a device wait on a flag nothing sets gave up after max_polls polls."""
+    g = _i32()
+    _check(lib().bs_selftest_bounded_wait(int(max_polls), ctypes.byref(g)), "bs_selftest_bounded_wait")
+    return bool(g.value)
 
 
 def bs_version() -> str:

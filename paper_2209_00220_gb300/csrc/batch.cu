@@ -44,6 +44,7 @@
 
 #include "lookup_dev.cuh"
 #include "scan_dev.cuh"
+#include "wait_dev.cuh"
 
 namespace bs {
 namespace {
@@ -179,12 +180,6 @@ __device__ __forceinline__ void gather_any(const LookK &a, uint32_t c, uint64_t 
     }
 }
 
-__device__ __forceinline__ uint32_t ld_acquire32(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 // Grid-wide barrier number `round` (1, 2, ...): every CTA adds one arrival and
 // waits until all gridDim.x * round arrivals are in.
 __device__ void grid_barrier(const BatchK &b, uint32_t round) {
@@ -192,15 +187,7 @@ __device__ void grid_barrier(const BatchK &b, uint32_t round) {
     if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(b.ctr + 2, 1u);
-        const uint32_t target = gridDim.x * round;
-        uint32_t spins = 0;
-        while (ld_acquire32(b.ctr + 2) < target) {
-            if (++spins > (1u << 24)) {
-                atomicOr(b.status, kStatusTimeout);
-                break;
-            }
-            __nanosleep(64);
-        }
+        bounded_wait_geq(b.ctr + 2, gridDim.x * round, 1u << 24, b.status);
         __threadfence();
     }
     __syncthreads();
