@@ -683,6 +683,73 @@ def run_ours(args):
     return 0
 
 
+# --------------------------------------------------- the full layout sweep
+SWEEP_WIDTHS = (8, 12, 16, 20, 24, 32)
+SWEEP_SKEWS = (0.0, 0.5, 1.0, 1.5)           # 0.0: uniform
+SWEEP_OPS = ("lt", "eq", "between")
+SWEEP_TARGETS = (0.001, 0.01, 0.1, 0.5, 0.9)
+
+
+def run_sweep(args):
+    """Every point of the single-column layout sweep (code widths x value
+    distributions x layouts x predicates x target selectivities) on one column
+    length: scan and lookup times, scan bytes and roofline fraction, one JSON
+    line per point, then one summary line per layout. Scan bytes replay every
+    16th tile (bs_scan_bytes_sampled) to bound the host time."""
+    import torch
+    from paper_2209_00220_gb300 import bytestore as B, synth
+    hbm, _ = _peaks()
+    n = args.rows
+    stream = torch.cuda.current_stream()
+    bits = torch.empty((n + 31) // 32, dtype=torch.int32, device="cuda")
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=5):
+        fn()
+        ts = []
+        for _ in range(reps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    summary = {}
+    for d in SWEEP_WIDTHS:
+        for s in SWEEP_SKEWS:
+            v = synth.config_sweep_column(n, d, s, d * 10 + int(s * 2))
+            for lay in ("bitpacked", "byteslice", "ppvbs"):
+                opts = {} if lay == "ppvbs" else {"domain_bits": d, "domain_min": synth.domain_min_for_bits(d)}
+                col = B.bs_encode_column(v, lay, keep_host=True, **opts)
+                ws = torch.empty(B.bs_lookup_workspace_bytes(col) // 4 + 1, dtype=torch.int32, device="cuda")
+                for op in SWEEP_OPS:
+                    for tgt in SWEEP_TARGETS:
+                        a, b = synth.pick_literals(v, op, tgt, 7)
+                        t_scan = timed(lambda: B.bs_scan(col, op, a, b, out=bits, stream=stream))
+                        t_look = timed(lambda: B.bs_lookup(col, bits, out=out, count=cnt, workspace=ws,
+                                                           stream=stream))
+                        m = int(cnt.item())
+                        by = B.bs_scan_bytes(col, op, a, b, stride=16)["bytes"]
+                        frac = by / (t_scan / 1e3) / 1e9 / hbm
+                        print(json.dumps({"d": d, "s": s, "layout": lay, "op": op, "target": tgt,
+                                          "selectivity": round(m / n, 5), "scan_ms": round(t_scan, 4),
+                                          "scan_frac": round(frac, 4), "scan_bytes_per_row": round(by / n, 4),
+                                          "lookup_ms": round(t_look, 4)}), flush=True)
+                        summary.setdefault(lay, []).append((frac, t_scan, t_look))
+                del col, ws
+    for lay, pts in summary.items():
+        f = np.array([p[0] for p in pts])
+        print(json.dumps({"summary": lay, "points": len(pts), "scan_frac_mean": round(float(f.mean()), 4),
+                          "scan_frac_median": round(float(np.median(f)), 4),
+                          "scan_frac_p10": round(float(np.percentile(f, 10)), 4),
+                          "scan_ms_total": round(float(sum(p[1] for p in pts)), 2),
+                          "lookup_ms_total": round(float(sum(p[2] for p in pts)), 2), "rows": n}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -696,9 +763,13 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-request batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-scale", type=float, default=1.0, help="serving table lengths x this factor")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the step: every point of the layout sweep, one JSON line each")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 

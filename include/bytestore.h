@@ -262,6 +262,12 @@ typedef struct {
 int bs_scan_bytes(const bs_column *col, bs_op op, int32_t lit, int32_t lit2, const uint32_t *h_seed,
                   bs_scan_bytes_t *out);
 
+/* bs_scan_bytes replaying every tile_stride-th tile only and scaling the
+ * counts up by the tiles skipped (sampled_tiles says how many were replayed);
+ * tile_stride = 1 is bs_scan_bytes. */
+int bs_scan_bytes_sampled(const bs_column *col, bs_op op, int32_t lit, int32_t lit2, const uint32_t *h_seed,
+                          uint64_t tile_stride, bs_scan_bytes_t *out);
+
 /* Bytes one lookup must move: the bit vector once, 4 bytes per output value and
  * the distinct sectors of every gathered byte, mask group and offset entry
  * (decode tables are assumed cache-resident). h_bits: host bit vector. */

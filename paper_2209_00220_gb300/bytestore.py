@@ -113,6 +113,7 @@ _SIGS = {
     "bs_column_load": ([ctypes.c_char_p, _vp, _vp], _i32),
     "bs_scan_bytes": ([_vp, _i32, _i32, _i32, _vp, _vp], _i32),
     "bs_lookup_bytes": ([_vp, _vp, _vp], _i32),
+    "bs_scan_bytes_sampled": ([_vp, _i32, _i32, _i32, _vp, _u64, _vp], _i32),
     "bs_batch_create": ([_vp, _i32, _vp, _vp], _i32),
     "bs_batch_launch": ([_vp, _vp], _i32),
     "bs_batch_info": ([_vp, _vp, _vp, _vp], _i32),
@@ -412,13 +413,18 @@ def _struct_dict(st) -> dict:
     return out
 
 
-def bs_scan_bytes(col: Column, op: str, lit: int, lit2: int = 0, seed=None) -> dict:
+def bs_scan_bytes(col: Column, op: str, lit: int, lit2: int = 0, seed=None, stride: int = 1) -> dict:
     """Bytes the scan must move at the kernels' granularity (host replay).
-    seed: optional host numpy uint32 bit vector."""
+    seed: optional host numpy uint32 bit vector; stride > 1 replays every
+    stride-th tile and scales up."""
     r = bs_scan_bytes_t()
     sd = None if seed is None else _np(seed, np.uint32)
-    _check(lib().bs_scan_bytes(col.handle, OPS[op], int(lit), int(lit2), None if sd is None else sd.ctypes.data,
-                               ctypes.byref(r)), "bs_scan_bytes")
+    sp = None if sd is None else sd.ctypes.data
+    if stride == 1:
+        _check(lib().bs_scan_bytes(col.handle, OPS[op], int(lit), int(lit2), sp, ctypes.byref(r)), "bs_scan_bytes")
+    else:
+        _check(lib().bs_scan_bytes_sampled(col.handle, OPS[op], int(lit), int(lit2), sp, int(stride),
+                                           ctypes.byref(r)), "bs_scan_bytes_sampled")
     return _struct_dict(r)
 
 
