@@ -165,9 +165,8 @@ __device__ __forceinline__ int32_t decode_value(const LookK &a, uint64_t code, i
 template <int KMAX>
 struct __align__(16) WarpSmemT {
     uint8_t dense[kTileRows];         // staged BS_1 of the tile
-    uint32_t seg[KMAX <= 4 ? kTileRows / 4 + 4 : 4];  // staged BS_2 segment (dense path, KMAX <= 4)
-    uint16_t list[kTileRows];         // sparse path: selected rows; dense path: decode keys
-    uint32_t skip[kTileWords];        // dense path: entries already written
+    uint32_t seg[KMAX == 2 ? kTileRows / 4 + 4 : 4];  // staged BS_2 segment (dense tiles, codes <= 2 bytes)
+    uint16_t list[kTileRows];         // selected rows of the tile (tile-local indices)
     uint32_t mask[KMAX + 1][kTileWords];
     uint32_t pref[KMAX + 1][kTileWords];
 };
@@ -223,73 +222,6 @@ __device__ __forceinline__ void fetch_code(const LookK &a, uint64_t t, uint32_t 
     }
 }
 
-// Dense PP-VBS tile: BS_1 and the tile's BS_2 segment are staged in shared
-// memory; each lane walks its own selected rows in order and leaves a 16-bit
-// decode key (first two code bytes) per output slot, codes of three or more
-// bytes being decoded on the spot; the warp then decodes the keys and writes
-// the values with coalesced stores.
-template <int KMAX>
-__device__ __forceinline__ void gather_dense_vbs(const LookK &a, uint64_t t, uint32_t sel, uint32_t excl,
-                                                 uint32_t total, int levels, uint64_t out_base, WarpSmemT<KMAX> &sm,
-                                                 const int32_t *val1, uint32_t lane) {
-    uint32_t seg_lo = 0;
-    if (levels >= 2) {
-        // BS_2 bytes of this tile are contiguous: [off_2[first group], off_2[first group of next tile])
-        seg_lo = __ldg(a.off[2] + t * kGroupsPerTile);
-        const uint32_t seg_hi = __ldg(a.off[2] + t * kGroupsPerTile + kGroupsPerTile);
-        const uint32_t w0 = seg_lo >> 2, w1 = (seg_hi + 3) >> 2;
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(a.deep[2]);
-        constexpr uint32_t kSegWords = sizeof(sm.seg) / 4;
-        for (uint32_t i = lane; i < w1 - w0 && i < kSegWords; i += 32) sm.seg[i] = __ldg(src + w0 + i);
-    }
-    sm.skip[lane] = 0u;
-    __syncwarp();
-    const uint8_t *seg = reinterpret_cast<const uint8_t *>(sm.seg) + (seg_lo & 3u);
-    const uint32_t m2 = levels >= 2 ? sm.mask[2][lane] : 0u;
-    const uint32_t p2 = levels >= 2 ? sm.pref[2][lane] - seg_lo : 0u;
-    const uint32_t m3 = (KMAX >= 3 && levels >= 3) ? sm.mask[KMAX >= 3 ? 3 : 2][lane] : 0u;
-    uint32_t pos = excl, r = sel;
-    while (r) {
-        const uint32_t b = __ffs(r) - 1, below = (1u << b) - 1u;
-        r &= r - 1;
-        const uint32_t q = lane * 32u + b;
-        const uint32_t c1 = sm.dense[q];
-        uint32_t key = c1 << 8;
-        if ((m2 >> b) & 1u) {
-            key |= seg[p2 + __popc(m2 & below)];
-            if (KMAX >= 3 && ((m3 >> b) & 1u)) {  // three or more bytes: decode now
-                uint64_t code;
-                int len;
-                fetch_code<BS_PPVBS, KMAX>(a, t, q, levels, &sm, true, code, len);
-                const uint64_t o = out_base + pos;
-                if (o < a.out_cap) a.out_vals[o] = decode_value<BS_PPVBS>(a, code, len);
-                atomicOr(&sm.skip[pos >> 5], 1u << (pos & 31));
-            }
-        }
-        sm.list[pos++] = (uint16_t)key;
-    }
-    __syncwarp();
-    for (uint32_t i0 = 0; i0 < total; i0 += 32 * kUnroll) {
-        int32_t v[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
-            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
-            v[u] = 0;
-            if (i < total) {
-                const uint32_t key = sm.list[i];
-                v[u] = (key & 0xFFu) ? __ldg(a.val2 + key) : val1[key >> 8];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
-            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
-            const uint64_t o = out_base + i;
-            if (i < total && o < a.out_cap && !((sm.skip[i >> 5] >> (i & 31)) & 1u)) a.out_vals[o] = v[u];
-        }
-    }
-    __syncwarp();
-}
-
 template <int LAYOUT, bool CODES, int KMAX>
 __device__ __forceinline__ void gather_tile(const LookK &a, uint64_t t, uint32_t sel, uint64_t out_base,
                                             WarpSmemT<KMAX> &sm, const int32_t *val1, uint32_t lane) {
@@ -302,9 +234,7 @@ __device__ __forceinline__ void gather_tile(const LookK &a, uint64_t t, uint32_t
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     if (total == 0) return;
-    constexpr bool kDenseOk = LAYOUT == BS_PPVBS && !CODES && KMAX <= 4;
-    const bool dense = kDenseOk && total >= kStageMin;
-    if (!dense) {
+    {
         uint32_t pos = incl - cnt, r = sel;
         while (r) {
             const uint32_t b = __ffs(r) - 1;
@@ -348,10 +278,6 @@ __device__ __forceinline__ void gather_tile(const LookK &a, uint64_t t, uint32_t
         }
     }
     __syncwarp();
-    if (kDenseOk && dense) {
-        gather_dense_vbs<KMAX>(a, t, sel, incl - cnt, total, levels, out_base, sm, val1, lane);
-        return;
-    }
     for (uint32_t i0 = 0; i0 < total; i0 += 32 * kUnroll) {
         uint64_t code[kUnroll];
         int len[kUnroll];
@@ -466,27 +392,25 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
     const uint64_t room = a.out_cap > out_base ? a.out_cap - out_base : 0;
     const uint32_t lim = (uint32_t)(room < total ? room : total);
     int32_t *dst = a.out_vals + out_base;
-    for (uint32_t i0 = 0; i0 < lim; i0 += 32 * kUnroll) {
+    auto value_of = [&](uint32_t i) -> int32_t {
+        const uint32_t q = sm.list[i], w = q >> 5, b = q & 31u;
+        const uint32_t mw = sm.mask[2][w];
+        const uint32_t c1 = sm.dense[q];
+        const uint32_t c2b = seg[sm.pref[2][w] + __popc(mw & ((1u << b) - 1u))];
+        const uint32_t key = (c1 << 8) | (((mw >> b) & 1u) ? c2b : 0u);
+        return (key & 0xFFu) ? __ldg(a.val2 + key) : val1[c1];
+    };
+    // whole rounds of 32 * kUnroll slots (kUnroll loads in flight per lane),
+    // then the remaining slots 32 at a time
+    uint32_t i0 = 0;
+    for (; i0 + 32u * kUnroll <= lim; i0 += 32u * kUnroll) {
         int32_t v[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
-            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
-            v[u] = 0;
-            if (i < lim) {
-                const uint32_t q = sm.list[i], w = q >> 5, b = q & 31u;
-                const uint32_t mw = sm.mask[2][w];
-                const uint32_t c1 = sm.dense[q];
-                const uint32_t c2b = seg[sm.pref[2][w] + __popc(mw & ((1u << b) - 1u))];
-                const uint32_t key = (c1 << 8) | (((mw >> b) & 1u) ? c2b : 0u);
-                v[u] = (key & 0xFFu) ? __ldg(a.val2 + key) : val1[c1];
-            }
-        }
+        for (int u = 0; u < kUnroll; u++) v[u] = value_of(i0 + (uint32_t)u * 32u + lane);
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
-            const uint32_t i = i0 + (uint32_t)u * 32u + lane;
-            if (i < lim) dst[i] = v[u];
-        }
+        for (int u = 0; u < kUnroll; u++) dst[i0 + (uint32_t)u * 32u + lane] = v[u];
     }
+    for (uint32_t i = i0 + lane; i < lim; i += 32u) dst[i] = value_of(i);
     __syncwarp();
 }
 
