@@ -365,7 +365,22 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
         const uint32_t w0 = seg_lo >> 2, w1 = (seg_hi + 3) >> 2;
         const uint32_t *s32 = reinterpret_cast<const uint32_t *>(a.deep[2]);
         constexpr uint32_t kSegWords = sizeof(sm.seg) / 4;
-        for (uint32_t i = lane; i < w1 - w0 && i < kSegWords; i += 32) sm.seg[i] = __ldg(s32 + w0 + i);
+        // up to four words per lane in flight at once (a segment of up to
+        // 512 bytes, the usual case, is one round)
+        const uint32_t nseg = min(w1 - w0, kSegWords);
+        for (uint32_t i0 = 0; i0 < nseg; i0 += 32u * kUnroll) {
+            uint32_t r[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+                r[u] = i < nseg ? __ldg(s32 + w0 + i) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+                if (i < nseg) sm.seg[i] = r[u];
+            }
+        }
     }
     uint4 r0, r1;
     transpose_lane_bytes(v0, v1, r0, r1);
@@ -543,19 +558,6 @@ __device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_
                 const uint32_t e = (uint32_t)tt * kGroupsPerTile;
                 const uint32_t goff = off_entry(e + (lane >> 3));
                 const uint32_t lo = off_entry(e), hi = off_entry(e + kGroupsPerTile);
-                const uint32_t tc1 = kHoist && tt + 1 < kChunkTiles ? __shfl_sync(kFull, tcl, (tt + 1) & 31) : 0u;
-                if (tc1 >= kStageMin && t + 1 < a.n_tiles) {
-                    // the next tile is dense too: its bytes into L2 while this
-                    // one is resolved -- BS_1 (lanes 0..7), M_2 (lane 8), the
-                    // start of its BS_2 segment (lanes 9..12), a 128-byte line each
-                    const uint32_t nlo = hi;
-                    const uint8_t *pa = nullptr;
-                    if (lane < 8u) pa = a.dense + (t + 1) * kTileRows + lane * 128u;
-                    else if (lane == 8u && a.K >= 2) pa = reinterpret_cast<const uint8_t *>(a.mask[2] + (t + 1) * kTileWords);
-                    else if (lane >= 9u && lane < 13u && a.K >= 2 && (uint64_t)nlo + (lane - 9u) * 128u < a.deep_len[2])
-                        pa = a.deep[2] + (uint64_t)nlo + (lane - 9u) * 128u;
-                    if (pa) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
-                }
                 gather_dense_k2(a, t, sel, base, goff, lo, hi, reinterpret_cast<WarpSmemT<2> &>(sm), val1, lane);
             } else {
                 gather_tile<LAYOUT, CODES, KMAX>(a, t, sel, base, sm, val1, lane);
