@@ -412,8 +412,8 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
         const uint32_t mw = sm.mask[2][w];
         const uint32_t c1 = sm.dense[q];
         const uint32_t c2b = seg[sm.pref[2][w] + __popc(mw & ((1u << b) - 1u))];
-        const uint32_t key = (c1 << 8) | (((mw >> b) & 1u) ? c2b : 0u);
-        return (key & 0xFFu) ? __ldg(a.val2 + key) : val1[c1];
+        const uint32_t c2 = ((mw >> b) & 1u) ? c2b : 0u;  // 0: a one-byte code
+        return c2 ? __ldg(a.val2 + ((c1 << 8) | c2)) : val1[c1];
     };
     // whole rounds of 32 * kUnroll slots (kUnroll loads in flight per lane),
     // then the remaining slots 32 at a time

@@ -52,18 +52,20 @@ __global__ void __launch_bounds__(kScanThreads, 8) scan_dense_kernel(const ScanK
     };
     issue(gw, 0);
     issue(gw + nw, 1);
-    int stage = 0;
+    int stage = 0, stage2 = 2;
+    const uint32_t full_tiles = (uint32_t)(a.n / kTileRows);
     for (uint32_t t = gw; t < a.n_tiles; t += nw) {
-        issue(t + 2 * nw, (stage + 2) % kStages);
+        issue(t + 2 * nw, stage2);
         cp_async_wait<kStages - 1>();
         const uint8_t *slot = my + stage * kSlot;
         const uint4 *sp = reinterpret_cast<const uint4 *>(slot);
         const uint4 v0 = sp[lane], v1 = sp[32 + lane];
         const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
         const uint32_t m2 = PF ? reinterpret_cast<const uint32_t *>(slot + kTileRows)[lane] : 0u;
-        const uint32_t sd = valid_mask(((uint64_t)t * kTileWords + lane) * 32u, a.n);
+        const uint32_t sd = t < full_tiles ? kFull : valid_mask(((uint64_t)t * kTileWords + lane) * 32u, a.n);
         scan_tile<VBS, NLIT, HI0, HI1, NEED_EQ, PF>(a, t, lane, x, sd, add0, add1, m2);
-        stage = (stage + 1) % kStages;
+        stage = stage == kStages - 1 ? 0 : stage + 1;
+        stage2 = stage2 == kStages - 1 ? 0 : stage2 + 1;
     }
     cp_async_wait<0>();
 }

@@ -78,6 +78,7 @@ struct ScanK {
     DLit lit[2];
     uint64_t lo, hi;           // Bit-Packed: code range of the predicate
     int32_t invert;            // Bit-Packed: result = !(lo <= code <= hi)
+    uint32_t fin_l, fin_e, fin_i;  // one literal: result = ((LT & fin_l) | (EQ & fin_e)) ^ (valid & fin_i), all-ones or zero each
     const uint32_t *seed;
     uint32_t *out;
     uint32_t *status;
@@ -156,19 +157,6 @@ __device__ __forceinline__ void load_lane32(const uint8_t *tile, uint32_t lane, 
     uint4 v1 = ld_stream_v4(tile + 512u + lane * 16u);
     x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
     x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
-}
-
-__device__ __forceinline__ uint32_t final_bits(int op, uint32_t sd, uint32_t LT1, uint32_t EQ1, uint32_t LT2,
-                                               uint32_t EQ2) {
-    switch (op) {
-    case BS_LT: return LT1;
-    case BS_LE: return LT1 | EQ1;
-    case BS_GT: return sd & ~(LT1 | EQ1);
-    case BS_GE: return sd & ~LT1;
-    case BS_EQ: return EQ1;
-    case BS_NE: return sd & ~EQ1;
-    default: return sd & ~LT1 & (LT2 | EQ2);  // BETWEEN
-    }
 }
 
 // ------------------------------------------------------- PP-VBS levels >= 2
@@ -307,7 +295,10 @@ __device__ __forceinline__ uint32_t scan_tile(const ScanK &a, uint32_t t, uint32
         }
     }
     const uint64_t w = (uint64_t)t * kTileWords + lane;
-    const uint32_t res = final_bits(a.op, sd, LT1, EQ1, LT2, EQ2);
+    // the op from the fully resolved (LT, EQ) masks: BETWEEN keeps rows not
+    // below c1 and not above c2; one literal picks LT and/or EQ and, for >, >=
+    // and !=, complements within the valid rows (LT and EQ are subsets of them)
+    const uint32_t res = NLIT == 2 ? (sd & ~LT1 & (LT2 | EQ2)) : (((LT1 & a.fin_l) | (EQ1 & a.fin_e)) ^ (sd & a.fin_i));
     if (a.out && w * 32u < a.n) st_stream(a.out + w, res);
     return res;
 }
@@ -386,6 +377,14 @@ inline void plan_scan(const Column &c, const KPred &p, const uint32_t *d_seed, b
     a.n_tiles = c.n_tiles;
     a.seed = d_seed;
     a.op = p.op;
+    {  // < : LT; <= : LT|EQ; > : valid & ~(LT|EQ); >= : valid & ~LT; = : EQ; != : valid & ~EQ
+        const bool L = p.op == BS_LT || p.op == BS_LE || p.op == BS_GT || p.op == BS_GE;
+        const bool E = p.op == BS_LE || p.op == BS_GT || p.op == BS_EQ || p.op == BS_NE;
+        const bool I = p.op == BS_GT || p.op == BS_GE || p.op == BS_NE;
+        a.fin_l = L ? 0xFFFFFFFFu : 0u;
+        a.fin_e = E ? 0xFFFFFFFFu : 0u;
+        a.fin_i = I ? 0xFFFFFFFFu : 0u;
+    }
     if (p.mode != Pred::kNormal) {
         a.fill_all = p.mode == Pred::kAll;
         plan.kind = ScanPlan::kFill;
