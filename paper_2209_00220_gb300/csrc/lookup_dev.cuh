@@ -23,7 +23,10 @@
 // and prefix-sums their popcounts into shared memory; a selected row's length
 // and the address of each of its bytes then come from shared memory alone, so
 // all its byte loads are issued together. A tile with many selected rows first
-// copies its 1 KB of BS_1 into shared memory with coalesced 16-byte loads.
+// copies its 1 KB of BS_1 into shared memory with coalesced 16-byte loads;
+// for columns whose codes have at most four bytes (Algorithm 1) it also stages
+// its BS_2 segment and takes M_2.. and the BS_j group offsets in the same round
+// of loads, so a slot costs shared-memory reads plus its own longer bytes.
 // Codes of at most two bytes decode with one table load (value by first two
 // bytes); longer codes sit in level-2 leaves whose values have consecutive
 // dictionary indices, decoded as dict[leaf start + rest - 1].
@@ -165,7 +168,7 @@ __device__ __forceinline__ int32_t decode_value(const LookK &a, uint64_t code, i
 template <int KMAX>
 struct __align__(16) WarpSmemT {
     uint8_t dense[kTileRows];         // staged BS_1 of the tile
-    uint32_t seg[KMAX == 2 ? kTileRows / 4 + 4 : 4];  // staged BS_2 segment (dense tiles, codes <= 2 bytes)
+    uint32_t seg[KMAX <= 4 ? kTileRows / 4 + 4 : 4];  // staged BS_2 segment (dense tiles, codes <= 4 bytes)
     uint16_t list[kTileRows];         // selected rows of the tile (tile-local indices)
     uint32_t mask[KMAX + 1][kTileWords];
     uint32_t pref[KMAX + 1][kTileWords];
@@ -429,6 +432,118 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
     __syncwarp();
 }
 
+// Dense PP-VBS tile of a column with codes of three or four bytes (Algorithm
+// 1): as for two-byte codes, BS_1 and the tile's BS_2 segment are staged and
+// every slot is resolved from shared memory up to its second byte; M_3 / M_4
+// and the group offsets of BS_3 / BS_4 come with the same round of loads, so a
+// longer code adds only its own byte loads. Codes of up to two bytes decode by
+// the one- and two-byte tables, longer ones as dict[leaf2[first two bytes] +
+// rest - 1] (indices clamped into the arrays whatever the bytes hold).
+__device__ __forceinline__ void gather_dense_k4(const LookK &a, uint64_t t, uint32_t sel, uint64_t out_base,
+                                                WarpSmemT<4> &sm, const int32_t *val1, uint32_t lane) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(a.dense + t * kTileRows);
+    const uint4 v0 = __ldg(src + lane), v1 = __ldg(src + 32 + lane);
+    const uint64_t w = t * kTileWords + lane, g = t * kGroupsPerTile;
+    const bool has4 = a.K >= 4;
+    const uint32_t m2 = __ldg(a.mask[2] + w), m3 = __ldg(a.mask[3] + w), m4 = has4 ? __ldg(a.mask[4] + w) : 0u;
+    const uint32_t seg_lo = __ldg(a.off[2] + g), seg_hi = __ldg(a.off[2] + g + kGroupsPerTile);
+    const uint32_t go2 = __ldg(a.off[2] + g + (lane >> 3)), go3 = __ldg(a.off[3] + g + (lane >> 3));
+    const uint32_t go4 = has4 ? __ldg(a.off[4] + g + (lane >> 3)) : 0u;
+    const uint32_t cnt = __popc(sel);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, d);
+        if (lane >= (uint32_t)d) incl += v;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    // exclusive prefix of the mask popcounts inside each 256-row group
+    auto group_excl = [&](uint32_t m) -> uint32_t {
+        const uint32_t c = __popc(m);
+        uint32_t inc = c;
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, inc, d);
+            if ((lane & 7u) >= (uint32_t)d) inc += v;
+        }
+        return inc - c;
+    };
+    const uint32_t p2 = go2 + group_excl(m2) - seg_lo, p3 = go3 + group_excl(m3), p4 = go4 + group_excl(m4);
+    {
+        const uint32_t w0 = seg_lo >> 2, w1 = (seg_hi + 3) >> 2;
+        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(a.deep[2]);
+        constexpr uint32_t kSegWords = sizeof(sm.seg) / 4;
+        const uint32_t nseg = min(w1 - w0, kSegWords);
+        for (uint32_t i0 = 0; i0 < nseg; i0 += 32u * kUnroll) {
+            uint32_t r[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+                r[u] = i < nseg ? __ldg(s32 + w0 + i) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const uint32_t i = i0 + (uint32_t)u * 32u + lane;
+                if (i < nseg) sm.seg[i] = r[u];
+            }
+        }
+    }
+    uint4 r0, r1;
+    transpose_lane_bytes(v0, v1, r0, r1);
+    uint4 *rows = reinterpret_cast<uint4 *>(sm.dense + lane * 32u);
+    rows[0] = r0;
+    rows[1] = r1;
+    sm.mask[2][lane] = m2;
+    sm.pref[2][lane] = p2;
+    sm.mask[3][lane] = m3;
+    sm.pref[3][lane] = p3;
+    sm.mask[4][lane] = m4;
+    sm.pref[4][lane] = p4;
+    uint32_t pos = incl - cnt, r = sel;
+    while (r) {
+        const uint32_t b = __ffs(r) - 1;
+        r &= r - 1;
+        sm.list[pos++] = (uint16_t)(lane * 32u + b);
+    }
+    __syncwarp();
+    const uint8_t *seg = reinterpret_cast<const uint8_t *>(sm.seg) + (seg_lo & 3u);
+    const uint64_t room = a.out_cap > out_base ? a.out_cap - out_base : 0;
+    const uint32_t lim = (uint32_t)(room < total ? room : total);
+    int32_t *dst = a.out_vals + out_base;
+    const uint64_t l3 = a.deep_len[3] ? a.deep_len[3] - 1 : 0, l4 = a.deep_len[4] ? a.deep_len[4] - 1 : 0;
+    const uint64_t dmax = a.dict_size ? a.dict_size - 1 : 0;
+    // no branches: every load is predicated on the row's length, so the
+    // kUnroll slots of a lane issue theirs together (byte 3 / 4, the two-byte
+    // table or the leaf start, then the dictionary)
+    auto value_of = [&](uint32_t i) -> int32_t {
+        const uint32_t q = sm.list[i], wq = q >> 5, b = q & 31u, below = (1u << b) - 1u;
+        const uint32_t c1 = sm.dense[q], mw2 = sm.mask[2][wq], mw3 = sm.mask[3][wq], mw4 = sm.mask[4][wq];
+        const bool has2 = (mw2 >> b) & 1u, has3 = (mw3 >> b) & 1u, has4 = (mw4 >> b) & 1u;
+        // the BS_2 index stays inside the staged segment even for a row
+        // without byte 2, so the read needs no guard of its own
+        const uint32_t key = (c1 << 8) | (has2 ? (uint32_t)seg[sm.pref[2][wq] + __popc(mw2 & below)] : 0u);
+        const uint64_t i3 = (uint64_t)sm.pref[3][wq] + __popc(mw3 & below);
+        const uint64_t i4 = (uint64_t)sm.pref[4][wq] + __popc(mw4 & below);
+        const uint32_t b3 = has3 ? __ldg(a.deep[3] + (i3 < l3 ? i3 : l3)) : 0u;
+        const uint32_t b4 = has4 ? __ldg(a.deep[4] + (i4 < l4 ? i4 : l4)) : 0u;
+        const int32_t v2 = has2 && !has3 ? __ldg(a.val2 + key) : 0;
+        const uint32_t leaf = has3 ? __ldg(a.leaf2 + key) : 0u;
+        const uint64_t di = (uint64_t)leaf + (has4 ? ((b3 << 8) | b4) : b3) - 1;
+        const int32_t vd = has3 ? __ldg(a.dict + (di < dmax ? di : dmax)) : 0;
+        return has3 ? vd : (has2 ? v2 : val1[c1]);
+    };
+    uint32_t i0 = 0;
+    for (; i0 + 32u * kUnroll <= lim; i0 += 32u * kUnroll) {
+        int32_t v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) v[u] = value_of(i0 + (uint32_t)u * 32u + lane);
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) dst[i0 + (uint32_t)u * 32u + lane] = v[u];
+    }
+    for (uint32_t i = i0 + lane; i < lim; i += 32u) dst[i] = value_of(i);
+    __syncwarp();
+}
+
 // One warp resolves chunk c (16 tiles) whose first output slot is `base`.
 // It reads the chunk's 512 bit vector words at once. A sparse chunk (at most
 // kSparseMax selected rows) lists its rows in shared memory and resolves them
@@ -518,6 +633,7 @@ __device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_
     // PP-VBS, codes <= 2 bytes: the chunk's 65 off_2 entries, two per lane
     // (entry e of the chunk at lane e / 2, the last one in every lane)
     constexpr bool kK2 = LAYOUT == BS_PPVBS && !CODES && KMAX == 2;
+    constexpr bool kK4 = LAYOUT == BS_PPVBS && !CODES && KMAX == 4;
     constexpr bool kHoist = HOIST && kK2;
     uint32_t offa = 0, offb = 0, offz = 0;
     const uint64_t e0 = (uint64_t)c * kChunkTiles * kGroupsPerTile;
@@ -559,6 +675,8 @@ __device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_
                 const uint32_t goff = off_entry(e + (lane >> 3));
                 const uint32_t lo = off_entry(e), hi = off_entry(e + kGroupsPerTile);
                 gather_dense_k2(a, t, sel, base, goff, lo, hi, reinterpret_cast<WarpSmemT<2> &>(sm), val1, lane);
+            } else if (kK4 && tc >= kStageMin && !a.categorical) {
+                gather_dense_k4(a, t, sel, base, reinterpret_cast<WarpSmemT<4> &>(sm), val1, lane);
             } else {
                 gather_tile<LAYOUT, CODES, KMAX>(a, t, sel, base, sm, val1, lane);
             }

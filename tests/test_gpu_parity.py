@@ -165,6 +165,43 @@ def test_scan_and_lookup_match_oracle(B, layout, name, values, extra):
     _check_clean(B)
 
 
+LONG_CODE_CASES = [
+    # (rows, code width d, Zipf s, monotone): K = 4 with every length 1..4 present
+    (300000, 24, 0.0, False),
+    (200000, 20, 1.0, True),
+    # K = 3, nearly all codes two bytes long
+    (250007, 16, 0.0, False),
+]
+
+
+@pytest.mark.parametrize("n,d,s,mono", LONG_CODE_CASES)
+def test_lookup_dense_tiles_long_codes(B, n, d, s, mono):
+    """Lookups of columns whose codes reach three or four bytes, at
+    selectivities that make every tile dense (the staged path) and sparse ones,
+    plus a capacity smaller than the count; the values equal the oracle's."""
+    import torch
+    v = synth.config_sweep_column(n, d, s, 40 + d, monotone=mono)
+    col = B.bs_encode_column(v, "ppvbs")
+    assert col.info()["max_code_bytes"] in (3, 4)
+    dec = orc.OracleColumn(v, "ppvbs").decode_values()
+    for op, t in (("lt", 0.05), ("lt", 0.5), ("ge", 0.2), ("gt", 0.9), ("ne", 0.01), ("eq", 0.01)):
+        a, _ = synth.pick_literals(v, op, t, 5)
+        bits = B.bs_scan(col, op, a)
+        sel = _bits(bits, n)
+        want = orc.lookup(dec, sel)
+        vals, cnt = B.bs_lookup(col, bits)
+        assert int(cnt.item()) == want.size
+        assert np.array_equal(vals[: want.size].cpu().numpy(), want), (op, t)
+        if want.size > 10:
+            cap = want.size // 3 + 1
+            out = torch.full((cap + 8,), -7, dtype=torch.int32, device="cuda")
+            vals, cnt = B.bs_lookup(col, bits, out=out, out_cap=cap)
+            got = out.cpu().numpy()
+            assert int(cnt.item()) == want.size
+            assert np.array_equal(got[:cap], want[:cap]) and np.all(got[cap:] == -7), (op, t)
+    _check_clean(B)
+
+
 @pytest.mark.parametrize("layout", ["ppvbs", "byteslice", "bitpacked"])
 def test_seeded_scans_and_conjunction(B, layout):
     import torch
