@@ -170,8 +170,8 @@ struct __align__(16) WarpSmemT {
     uint8_t dense[kTileRows];         // staged BS_1 of the tile
     uint32_t seg[KMAX <= 4 ? kTileRows / 4 + 4 : 4];  // staged BS_2 segment (dense tiles, codes <= 4 bytes)
     uint16_t list[kTileRows];         // selected rows of the tile (tile-local indices)
-    uint32_t mask[KMAX + 1][kTileWords];
-    uint32_t pref[KMAX + 1][kTileWords];
+    uint32_t mask[KMAX - 1][kTileWords];  // level j (2..KMAX) at j - 2
+    uint32_t pref[KMAX - 1][kTileWords];
 };
 
 static_assert(sizeof(WarpSmemT<2>) % 16 == 0 && sizeof(WarpSmemT<4>) % 16 == 0 && sizeof(WarpSmemT<8>) % 16 == 0,
@@ -189,14 +189,14 @@ __device__ __forceinline__ void fetch_code(const LookK &a, uint64_t t, uint32_t 
         len = 1;
 #pragma unroll
         for (int j = 2; j <= KMAX; j++)
-            if (j <= levels && len == j - 1 && ((sm->mask[j][wq] >> bq) & 1u)) len = j;
+            if (j <= levels && len == j - 1 && ((sm->mask[j - 2][wq] >> bq) & 1u)) len = j;
         uint32_t b[KMAX + 1];
         b[1] = staged ? (uint32_t)sm->dense[q] : (uint32_t)__ldg(a.dense + t * kTileRows + tile_pos(q));
 #pragma unroll
         for (int j = 2; j <= KMAX; j++) {
             b[j] = 0;
             if (j <= len) {
-                const uint64_t idx = (uint64_t)sm->pref[j][wq] + __popc(sm->mask[j][wq] & below);
+                const uint64_t idx = (uint64_t)sm->pref[j - 2][wq] + __popc(sm->mask[j - 2][wq] & below);
                 if (idx < a.deep_len[j]) b[j] = __ldg(a.deep[j] + idx);
                 else atomicOr(a.status, kStatusBounds);
             }
@@ -274,8 +274,8 @@ __device__ __forceinline__ void gather_tile(const LookK &a, uint64_t t, uint32_t
                 if ((lane & 7u) >= (uint32_t)d) inc += v;
             }
             const uint32_t goff = gact ? __ldg(a.off[j] + t * kGroupsPerTile + (lane >> 3)) : 0u;
-            sm.mask[j][lane] = m;
-            sm.pref[j][lane] = goff + inc - c;
+            sm.mask[j - 2][lane] = m;
+            sm.pref[j - 2][lane] = goff + inc - c;
             reach = sel & m;
             levels = j;
         }
@@ -392,8 +392,8 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
     rows[1] = r1;
     // per lane word: its M_2 bits and its first BS_2 byte, relative to the
     // staged segment
-    sm.mask[2][lane] = m2;
-    sm.pref[2][lane] = goff + inc2 - c2 - seg_lo;
+    sm.mask[0][lane] = m2;
+    sm.pref[0][lane] = goff + inc2 - c2 - seg_lo;
     // the lane's selected rows, in row order, at its output positions
     uint32_t pos = incl - cnt, r = sel;
     while (r) {
@@ -412,9 +412,9 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
     int32_t *dst = a.out_vals + out_base;
     auto value_of = [&](uint32_t i) -> int32_t {
         const uint32_t q = sm.list[i], w = q >> 5, b = q & 31u;
-        const uint32_t mw = sm.mask[2][w];
+        const uint32_t mw = sm.mask[0][w];
         const uint32_t c1 = sm.dense[q];
-        const uint32_t c2b = seg[sm.pref[2][w] + __popc(mw & ((1u << b) - 1u))];
+        const uint32_t c2b = seg[sm.pref[0][w] + __popc(mw & ((1u << b) - 1u))];
         const uint32_t c2 = ((mw >> b) & 1u) ? c2b : 0u;  // 0: a one-byte code
         return c2 ? __ldg(a.val2 + ((c1 << 8) | c2)) : val1[c1];
     };
@@ -493,12 +493,12 @@ __device__ __forceinline__ void gather_dense_k4(const LookK &a, uint64_t t, uint
     uint4 *rows = reinterpret_cast<uint4 *>(sm.dense + lane * 32u);
     rows[0] = r0;
     rows[1] = r1;
-    sm.mask[2][lane] = m2;
-    sm.pref[2][lane] = p2;
-    sm.mask[3][lane] = m3;
-    sm.pref[3][lane] = p3;
-    sm.mask[4][lane] = m4;
-    sm.pref[4][lane] = p4;
+    sm.mask[0][lane] = m2;
+    sm.pref[0][lane] = p2;
+    sm.mask[1][lane] = m3;
+    sm.pref[1][lane] = p3;
+    sm.mask[2][lane] = m4;
+    sm.pref[2][lane] = p4;
     uint32_t pos = incl - cnt, r = sel;
     while (r) {
         const uint32_t b = __ffs(r) - 1;
@@ -517,13 +517,13 @@ __device__ __forceinline__ void gather_dense_k4(const LookK &a, uint64_t t, uint
     // table or the leaf start, then the dictionary)
     auto value_of = [&](uint32_t i) -> int32_t {
         const uint32_t q = sm.list[i], wq = q >> 5, b = q & 31u, below = (1u << b) - 1u;
-        const uint32_t c1 = sm.dense[q], mw2 = sm.mask[2][wq], mw3 = sm.mask[3][wq], mw4 = sm.mask[4][wq];
+        const uint32_t c1 = sm.dense[q], mw2 = sm.mask[0][wq], mw3 = sm.mask[1][wq], mw4 = sm.mask[2][wq];
         const bool has2 = (mw2 >> b) & 1u, has3 = (mw3 >> b) & 1u, has4 = (mw4 >> b) & 1u;
         // the BS_2 index stays inside the staged segment even for a row
         // without byte 2, so the read needs no guard of its own
-        const uint32_t key = (c1 << 8) | (has2 ? (uint32_t)seg[sm.pref[2][wq] + __popc(mw2 & below)] : 0u);
-        const uint64_t i3 = (uint64_t)sm.pref[3][wq] + __popc(mw3 & below);
-        const uint64_t i4 = (uint64_t)sm.pref[4][wq] + __popc(mw4 & below);
+        const uint32_t key = (c1 << 8) | (has2 ? (uint32_t)seg[sm.pref[0][wq] + __popc(mw2 & below)] : 0u);
+        const uint64_t i3 = (uint64_t)sm.pref[1][wq] + __popc(mw3 & below);
+        const uint64_t i4 = (uint64_t)sm.pref[2][wq] + __popc(mw4 & below);
         const uint32_t b3 = has3 ? __ldg(a.deep[3] + (i3 < l3 ? i3 : l3)) : 0u;
         const uint32_t b4 = has4 ? __ldg(a.deep[4] + (i4 < l4 ? i4 : l4)) : 0u;
         const int32_t v2 = has2 && !has3 ? __ldg(a.val2 + key) : 0;
