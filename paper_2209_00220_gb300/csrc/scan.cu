@@ -18,7 +18,11 @@ template <bool VBS, int NLIT, bool HI0, bool HI1, bool NEED_EQ, bool PF>
 __global__ void __launch_bounds__(kScanThreads, 8) scan_dense_kernel(const ScanK a) {
     constexpr int kSlot = kTileRows + (PF ? kTileWords * 4 : 0);
     static_assert(kSlot % 16 == 0, "ring slots receive 16-byte cp.async copies");
-    __shared__ __align__(16) uint8_t ring[kScanWarps][kStages][kSlot];
+    // two slots per warp: the tile being resolved and the next one in flight
+    // (three measured 2-3 % slower: eight CTAs of three-slot rings take 221 KB
+    // of the SM's shared memory, of two-slot rings 147 KB, and the rest serves
+    // as L1 for the deeper bytes)
+    __shared__ __align__(16) uint8_t ring[kScanWarps][2][kSlot];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -37,7 +41,7 @@ __global__ void __launch_bounds__(kScanThreads, 8) scan_dense_kernel(const ScanK
         }
         return;
     }
-    // unseeded: 3-stage cp.async ring, two tiles in flight ahead of the one resolved
+    // unseeded: 2-slot cp.async ring, the warp's next tile in flight while one is resolved
     uint8_t *my = &ring[warp][0][0];
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(my);
     auto issue = [&](uint32_t t, int stage) {
@@ -51,12 +55,11 @@ __global__ void __launch_bounds__(kScanThreads, 8) scan_dense_kernel(const ScanK
         cp_async_commit();  // empty groups keep the group count uniform
     };
     issue(gw, 0);
-    issue(gw + nw, 1);
-    int stage = 0, stage2 = 2;
+    int stage = 0;
     const uint32_t full_tiles = (uint32_t)(a.n / kTileRows);
     for (uint32_t t = gw; t < a.n_tiles; t += nw) {
-        issue(t + 2 * nw, stage2);
-        cp_async_wait<kStages - 1>();
+        issue(t + nw, stage ^ 1);
+        cp_async_wait<1>();
         const uint8_t *slot = my + stage * kSlot;
         const uint4 *sp = reinterpret_cast<const uint4 *>(slot);
         const uint4 v0 = sp[lane], v1 = sp[32 + lane];
@@ -64,8 +67,7 @@ __global__ void __launch_bounds__(kScanThreads, 8) scan_dense_kernel(const ScanK
         const uint32_t m2 = PF ? reinterpret_cast<const uint32_t *>(slot + kTileRows)[lane] : 0u;
         const uint32_t sd = t < full_tiles ? kFull : valid_mask(((uint64_t)t * kTileWords + lane) * 32u, a.n);
         scan_tile<VBS, NLIT, HI0, HI1, NEED_EQ, PF>(a, t, lane, x, sd, add0, add1, m2);
-        stage = stage == kStages - 1 ? 0 : stage + 1;
-        stage2 = stage2 == kStages - 1 ? 0 : stage2 + 1;
+        stage ^= 1;
     }
     cp_async_wait<0>();
 }

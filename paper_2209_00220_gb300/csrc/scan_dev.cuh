@@ -31,10 +31,11 @@
 // settled (equal or larger: never smaller), so level l + 1 is not read; with a
 // one-byte literal the EQ mask is not even formed.
 //
-// Unseeded scans stream slice 1 through a 3-stage cp.async ring in shared
-// memory per warp, so two tiles are in flight while one is resolved. Each
-// lane reads back only the 32 bytes it copied itself, so no barrier is needed
-// beyond cp.async.wait_group.
+// Unseeded scans stream slice 1 through a cp.async ring in shared memory per
+// warp (two slots in the single-query kernel: the next tile is in flight while
+// one is resolved; kStages in the batched kernel). Each lane reads back only
+// the 32 bytes it copied itself, so no barrier is needed beyond
+// cp.async.wait_group.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -53,7 +54,7 @@ constexpr uint32_t kMsb = 0x80808080u;
 constexpr uint32_t kLow7 = 0x7F7F7F7Fu;
 constexpr int kScanThreads = 256;
 constexpr int kScanWarps = kScanThreads / 32;
-constexpr int kStages = 3;
+constexpr int kStages = 3;  // ring slots per warp in the batched kernel
 
 struct DLit {
     uint32_t len;      // bytes in the literal code
