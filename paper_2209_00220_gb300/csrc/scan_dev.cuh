@@ -207,44 +207,37 @@ __device__ __forceinline__ void vbs_deeper(const ScanK &a, uint32_t t, uint32_t 
             const uint64_t dlen = a.deep_len[j];
             const uint32_t c1 = lit_byte(a.lit[0], j);
             const uint32_t c2 = NLIT == 2 ? lit_byte(a.lit[1], j) : 0u;
-            uint32_t bits = need;
-            if (NLIT == 1) {
-                // one literal: every pending row is in EQ1; collect "less" and
-                // "differs" over the lane's pending rows, then apply once (the
-                // lane's BS_j bytes are the run [base, base + cnt))
-                if (base + cnt <= dlen) {
-                    const uint8_t *run = deep + base;
-                    uint32_t lt = 0u, ne = 0u;
-                    while (bits) {
-                        const uint32_t bit = bits & (0u - bits);
-                        bits ^= bit;
-                        const uint32_t byte = __ldg(run + __popc(mj & (bit - 1u)));
-                        lt |= byte < c1 ? bit : 0u;
-                        ne |= byte != c1 ? bit : 0u;
+            // collect "less" and "differs" against each literal over the
+            // lane's pending rows, then apply them once to the rows still
+            // equal to that literal (the lane's BS_j bytes are the run
+            // [base, base + cnt))
+            if (base + cnt <= dlen) {
+                const uint8_t *run = deep + base;
+                uint32_t bits = need, lt1 = 0u, ne1 = 0u, lt2 = 0u, ne2 = 0u;
+                while (bits) {
+                    const uint32_t bit = bits & (0u - bits);
+                    bits ^= bit;
+                    const uint32_t byte = __ldg(run + __popc(mj & (bit - 1u)));
+                    lt1 |= byte < c1 ? bit : 0u;
+                    ne1 |= byte != c1 ? bit : 0u;
+                    if (NLIT == 2) {
+                        lt2 |= byte < c2 ? bit : 0u;
+                        ne2 |= byte != c2 ? bit : 0u;
                     }
-                    LT1 |= lt;
-                    EQ1 &= ~ne;
+                }
+                if (NLIT == 1) {  // every pending row is still equal to the literal
+                    LT1 |= lt1;
+                    EQ1 &= ~ne1;
                 } else {
-                    atomicOr(a.status, kStatusBounds);
-                    bits = 0u;
+                    const uint32_t d1 = act1 && j <= l1 ? EQ1 & need : 0u;
+                    const uint32_t d2 = act2 && j <= l2 ? EQ2 & need : 0u;
+                    LT1 |= lt1 & d1;
+                    EQ1 &= ~(ne1 & d1);
+                    LT2 |= lt2 & d2;
+                    EQ2 &= ~(ne2 & d2);
                 }
-            }
-            while (bits) {
-                const uint32_t r = __ffs(bits) - 1;
-                const uint32_t bit = 1u << r;
-                bits &= bits - 1;
-                const uint64_t idx = base + __popc(mj & (bit - 1u));
-                uint32_t byte = 0;
-                if (idx < dlen) byte = __ldg(deep + idx);
-                else atomicOr(a.status, kStatusBounds);
-                if (act1 && j <= l1 && (EQ1 & bit)) {
-                    if (byte < c1) { LT1 |= bit; EQ1 &= ~bit; }
-                    else if (byte > c1) EQ1 &= ~bit;
-                }
-                if (act2 && j <= l2 && (EQ2 & bit)) {
-                    if (byte < c2) { LT2 |= bit; EQ2 &= ~bit; }
-                    else if (byte > c2) EQ2 &= ~bit;
-                }
+            } else {
+                atomicOr(a.status, kStatusBounds);
             }
         }
     }
