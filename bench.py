@@ -137,6 +137,45 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def _cpulist(text):
+    cpus = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        a, _, b = part.partition("-")
+        cpus.update(range(int(a), int(b or a) + 1))
+    return cpus
+
+
+def bind_near_gpu(local):
+    """Restricts this process to the CPUs of the NUMA node its GPU hangs off
+    (read from sysfs for the GPU's PCI address), so that pinned host buffers
+    allocated afterwards sit in that node's memory; host-to-device traffic then
+    avoids the link between CPU sockets. Returns the node, or None when it
+    cannot be determined (nothing changed)."""
+    try:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+        sel = vis[local].strip() if local < len(vis) and vis[local].strip() else str(local)
+        out = subprocess.run(["nvidia-smi", "-i", sel, "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=30).stdout.strip().splitlines()
+        if len(out) != 1:
+            return None
+        dom, rest = out[0].strip().split(":", 1)
+        bdf = "%04x:%s" % (int(dom, 16), rest.lower())
+        with open("/sys/bus/pci/devices/%s/numa_node" % bdf) as f:
+            node = int(f.read())
+        if node < 0:
+            return None
+        with open("/sys/devices/system/node/node%d/cpulist" % node) as f:
+            cpus = _cpulist(f.read()) & os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return node
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -517,8 +556,9 @@ def _scaled(full_traffic, n):
 
 
 def run_ours(args):
-    import torch
     ws, rank, local = _dist()
+    numa = bind_near_gpu(local)
+    import torch
     torch.cuda.set_device(local)
     dist = None
     if ws > 1:
@@ -639,7 +679,8 @@ def run_ours(args):
         "config": {"workload": "sweep column d=12 Zipf s=1.0 PP-VBS, v < c at 10% + lookup",
                    "rows_per_gpu": n, "selected": m, "selectivity": round(m / n, 5), "K": info["max_code_bytes"],
                    "l2": "inputs larger than L2 (BS_1 = %d MB), no flush" % (n >> 20),
-                   "parallelism": "row shards, replicas" if ws > 1 else "single GPU"},
+                   "parallelism": "row shards, replicas" if ws > 1 else "single GPU",
+                   "host_numa_node": numa},
         "scan_grows_s": round(n / scan_avg_s / 1e9, 3),
         "scan_ms": round(float(np.median(scan_ms)), 4),
         "lookup_gvals_s": round(m / (float(np.mean(look_ms)) / 1e3) / 1e9, 3),
