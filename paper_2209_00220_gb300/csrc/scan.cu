@@ -14,7 +14,7 @@ namespace {
 
 // PF: the tile's M_2 words travel in the ring with its BS_1 bytes (chosen on
 // the host when most tiles are expected to hold rows pending after byte 1).
-template <bool VBS, int NLIT, bool HI0, bool HI1, bool NEED_EQ, bool PF>
+template <bool VBS, int NLIT, bool HI0, bool HI1, bool NEED_EQ, bool PF, int HI23>
 __global__ void __launch_bounds__(kScanThreads, 8) scan_dense_kernel(const ScanK a) {
     constexpr int kSlot = kTileRows + (PF ? kTileWords * 4 : 0);
     static_assert(kSlot % 16 == 0, "ring slots receive 16-byte cp.async copies");
@@ -28,6 +28,8 @@ __global__ void __launch_bounds__(kScanThreads, 8) scan_dense_kernel(const ScanK
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t c0 = lit_byte(a.lit[0], 1);
     const uint32_t add0 = thr_add(c0), add1 = thr_add(c0 + 1);
+    const uint32_t c2 = lit_byte(a.lit[1], 1);
+    const uint32_t add2 = thr_add(c2), add3 = thr_add(c2 + 1);
 
     if (a.seed) {
         // seeded: lanes whose seed word is zero read nothing
@@ -37,7 +39,7 @@ __global__ void __launch_bounds__(kScanThreads, 8) scan_dense_kernel(const ScanK
             if (sd) sd &= __ldg(a.seed + w);
             uint32_t x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (sd) load_lane32(a.dense + (uint64_t)t * kTileRows, lane, x);
-            scan_tile<VBS, NLIT, HI0, HI1, NEED_EQ, false>(a, t, lane, x, sd, add0, add1, 0u);
+            scan_tile<VBS, NLIT, HI0, HI1, NEED_EQ, false, HI23>(a, t, lane, x, sd, add0, add1, 0u, add2, add3);
         }
         return;
     }
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(kScanThreads, 8) scan_dense_kernel(const ScanK
         const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
         const uint32_t m2 = PF ? reinterpret_cast<const uint32_t *>(slot + kTileRows)[lane] : 0u;
         const uint32_t sd = t < full_tiles ? kFull : valid_mask(((uint64_t)t * kTileWords + lane) * 32u, a.n);
-        scan_tile<VBS, NLIT, HI0, HI1, NEED_EQ, PF>(a, t, lane, x, sd, add0, add1, m2);
+        scan_tile<VBS, NLIT, HI0, HI1, NEED_EQ, PF, HI23>(a, t, lane, x, sd, add0, add1, m2, add2, add3);
         stage ^= 1;
     }
     cp_async_wait<0>();
@@ -133,14 +135,35 @@ template <bool VBS, int NLIT, bool PF>
 KernelFn pick_dense(bool hi0, bool hi1, bool need_eq) {
     const int sel = (hi0 ? 4 : 0) | (hi1 ? 2 : 0) | (need_eq ? 1 : 0);
     switch (sel) {
-    case 0: return scan_dense_kernel<VBS, NLIT, false, false, false, PF>;
-    case 1: return scan_dense_kernel<VBS, NLIT, false, false, true, PF>;
-    case 2: return scan_dense_kernel<VBS, NLIT, false, true, false, PF>;
-    case 3: return scan_dense_kernel<VBS, NLIT, false, true, true, PF>;
-    case 4: return scan_dense_kernel<VBS, NLIT, true, false, false, PF>;
-    case 5: return scan_dense_kernel<VBS, NLIT, true, false, true, PF>;
-    case 6: return scan_dense_kernel<VBS, NLIT, true, true, false, PF>;
-    default: return scan_dense_kernel<VBS, NLIT, true, true, true, PF>;
+    case 0: return scan_dense_kernel<VBS, NLIT, false, false, false, PF, -1>;
+    case 1: return scan_dense_kernel<VBS, NLIT, false, false, true, PF, -1>;
+    case 2: return scan_dense_kernel<VBS, NLIT, false, true, false, PF, -1>;
+    case 3: return scan_dense_kernel<VBS, NLIT, false, true, true, PF, -1>;
+    case 4: return scan_dense_kernel<VBS, NLIT, true, false, false, PF, -1>;
+    case 5: return scan_dense_kernel<VBS, NLIT, true, false, true, PF, -1>;
+    case 6: return scan_dense_kernel<VBS, NLIT, true, true, false, PF, -1>;
+    default: return scan_dense_kernel<VBS, NLIT, true, true, true, PF, -1>;
+    }
+}
+
+// BETWEEN: both literals' first-byte thresholds as compile-time constants
+template <bool VBS, bool PF, bool HI0, bool HI1>
+KernelFn pick_between_hi(bool hi2, bool hi3) {
+    switch ((hi2 ? 2 : 0) | (hi3 ? 1 : 0)) {
+    case 0: return scan_dense_kernel<VBS, 2, HI0, HI1, true, PF, 0>;
+    case 1: return scan_dense_kernel<VBS, 2, HI0, HI1, true, PF, 1>;
+    case 2: return scan_dense_kernel<VBS, 2, HI0, HI1, true, PF, 2>;
+    default: return scan_dense_kernel<VBS, 2, HI0, HI1, true, PF, 3>;
+    }
+}
+
+template <bool VBS, bool PF>
+KernelFn pick_between(bool hi0, bool hi1, bool hi2, bool hi3) {
+    switch ((hi0 ? 2 : 0) | (hi1 ? 1 : 0)) {
+    case 0: return pick_between_hi<VBS, PF, false, false>(hi2, hi3);
+    case 1: return pick_between_hi<VBS, PF, false, true>(hi2, hi3);
+    case 2: return pick_between_hi<VBS, PF, true, false>(hi2, hi3);
+    default: return pick_between_hi<VBS, PF, true, true>(hi2, hi3);
     }
 }
 
@@ -180,13 +203,13 @@ int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_
     KernelFn fn;
     if (plan.vbs) {
         if (plan.pf)
-            fn = plan.nlit == 2 ? pick_dense<true, 2, true>(plan.hi0, plan.hi1, true)
+            fn = plan.nlit == 2 ? pick_between<true, true>(plan.hi0, plan.hi1, plan.hi2, plan.hi3)
                                 : pick_dense<true, 1, true>(plan.hi0, plan.hi1, plan.eq1);
         else
-            fn = plan.nlit == 2 ? pick_dense<true, 2, false>(plan.hi0, plan.hi1, true)
+            fn = plan.nlit == 2 ? pick_between<true, false>(plan.hi0, plan.hi1, plan.hi2, plan.hi3)
                                 : pick_dense<true, 1, false>(plan.hi0, plan.hi1, plan.eq1);
     } else {
-        fn = plan.nlit == 2 ? pick_dense<false, 2, false>(plan.hi0, plan.hi1, true)
+        fn = plan.nlit == 2 ? pick_between<false, false>(plan.hi0, plan.hi1, plan.hi2, plan.hi3)
                             : pick_dense<false, 1, false>(plan.hi0, plan.hi1, plan.eq1);
     }
     fn<<<grid_for(fn, c.n_tiles, dev), kScanThreads, 0, s>>>(a);

@@ -270,15 +270,25 @@ __device__ __forceinline__ void bsl_deeper(const ScanK &a, uint32_t t, uint32_t 
 }
 
 // One tile whose lane bytes are in x: byte 1, deeper levels, result word.
-template <bool VBS, int NLIT, bool HI0, bool HI1, bool NEED_EQ, bool PF>
+// HI23 (BETWEEN): bit 1 / bit 0 = high bit of the upper literal's first byte
+// c2 / of c2 + 1 as compile-time constants (add2, add3 its thresholds), or -1
+// to compare against c2 with run-time thresholds.
+template <bool VBS, int NLIT, bool HI0, bool HI1, bool NEED_EQ, bool PF, int HI23 = -1>
 __device__ __forceinline__ uint32_t scan_tile(const ScanK &a, uint32_t t, uint32_t lane, const uint32_t x[8],
-                                          uint32_t sd, uint32_t add0, uint32_t add1, uint32_t m2_pre) {
+                                          uint32_t sd, uint32_t add0, uint32_t add1, uint32_t m2_pre,
+                                          uint32_t add2 = 0u, uint32_t add3 = 0u) {
     uint32_t GE1, EQ1 = 0, LT2 = 0, EQ2 = 0;
     cmp32_fast<HI0, HI1, NEED_EQ>(x, add0, add1, GE1, EQ1);
     uint32_t LT1 = sd & ~GE1;
     EQ1 &= sd;
     if (NLIT == 2) {
-        cmp32_rt(x, lit_byte(a.lit[1], 1), LT2, EQ2);
+        if constexpr (HI23 >= 0) {
+            uint32_t GE2;
+            cmp32_fast<(HI23 & 2) != 0, (HI23 & 1) != 0, true>(x, add2, add3, GE2, EQ2);
+            LT2 = ~GE2;
+        } else {
+            cmp32_rt(x, lit_byte(a.lit[1], 1), LT2, EQ2);
+        }
         LT2 &= sd;
         EQ2 &= sd;
     }
@@ -357,6 +367,7 @@ struct ScanPlan {
     bool vbs;         // dense: PP-VBS (else ByteSlice)
     int32_t nlit;     // 2 for BETWEEN
     bool hi0, hi1;    // high bits of the first literal byte c and of c + 1
+    bool hi2, hi3;    // BETWEEN: the same for the upper literal's first byte
     bool eq1;         // the EQ mask of byte 1 is needed
     bool pf;          // PP-VBS: prefetch M_2 with every tile
 };
@@ -441,6 +452,9 @@ inline void plan_scan(const Column &c, const KPred &p, const uint32_t *d_seed, b
     const uint32_t cb = (uint32_t)(a.lit[0].left >> 56);
     plan.hi0 = cb >= 128u;
     plan.hi1 = cb + 1 >= 128u;
+    const uint32_t cb2 = (uint32_t)(a.lit[1].left >> 56);
+    plan.hi2 = nlit == 2 && cb2 >= 128u;
+    plan.hi3 = nlit == 2 && cb2 + 1 >= 128u;
     // prefetch M_2 with every tile when rows sharing the literal's first byte are
     // common enough that nearly every tile has some (more than ~4 per tile)
     if (allow_pf && c.layout == BS_PPVBS && c.K >= 2 && plan.eq1 && !d_seed) {
