@@ -11,8 +11,9 @@
 //              writes the total of its 8 chunks;
 //   2. scan:   one CTA turns the CTA totals into exclusive offsets (coalesced
 //              segments of 4096) and writes the selected-row count;
-//   3. gather: one CTA per chunk; its offset is its CTA offset plus the counts
-//              of the chunks before it in the same group of 8. Per tile, a warp
+//   3. gather: persistent CTAs walk the groups of 8 chunks, one warp per
+//              chunk; a chunk's offset is its group's offset plus the counts
+//              of the chunks before it in the group. Per tile, a warp
 //              prefix-sums its 32 word popcounts, lists the selected rows in
 //              shared memory (ascending), and lanes take list entries
 //              round-robin, four at a time, so output writes are coalesced and
@@ -24,9 +25,10 @@
 // and the address of each of its bytes then come from shared memory alone, so
 // all its byte loads are issued together. A tile with many selected rows first
 // copies its 1 KB of BS_1 into shared memory with coalesced 16-byte loads;
-// for columns whose codes have at most four bytes (Algorithm 1) it also stages
-// its BS_2 segment and takes M_2.. and the BS_j group offsets in the same round
-// of loads, so a slot costs shared-memory reads plus its own longer bytes.
+// for columns whose codes have at most two bytes, or at most four bytes by
+// Algorithm 1, it also stages its BS_2 segment and takes M_2.. and the BS_j
+// group offsets in the same round of loads, so a slot costs shared-memory
+// reads plus its own longer bytes.
 // Codes of at most two bytes decode with one table load (value by first two
 // bytes); longer codes sit in level-2 leaves whose values have consecutive
 // dictionary indices, decoded as dict[leaf start + rest - 1].
