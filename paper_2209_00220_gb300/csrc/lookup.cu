@@ -85,8 +85,13 @@ __global__ void __launch_bounds__(kScanBlock) lookup_scan_kernel(const LookK a) 
 }
 
 // ------------------------------------------------------------ 3. gather
-// A CTA's 8 warps own the 8 chunks of one count group; the CTA walks groups
-// persistently (blockIdx.x, blockIdx.x + gridDim.x, ...).
+// Work units are (chunk, part): a chunk's 16 tiles are split over a.parts
+// warps (1 on columns with enough chunks to fill the GPU, up to 16 on short
+// ones). With one part a CTA's 8 warps own the 8 chunks of one count group;
+// CTAs walk the units persistently (blockIdx.x * 8 + warp, then + gridDim.x *
+// 8, ...). A unit's first output slot is its group's offset plus the counts of
+// the chunks before it in the group (plus, inside gather_chunk, the counts of
+// the chunk's earlier tiles).
 template <int LAYOUT, bool CODES, int KMAX>
 __global__ void __launch_bounds__(kLookupThreads, 5) lookup_gather_kernel(const LookK a) {
     __shared__ WarpSmemT<KMAX> smem[kLookupWarps];
@@ -94,13 +99,16 @@ __global__ void __launch_bounds__(kLookupThreads, 5) lookup_gather_kernel(const 
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     if (LAYOUT == BS_PPVBS && !CODES && threadIdx.x < 256) val1[threadIdx.x] = __ldg(a.val2 + (threadIdx.x << 8));
     __syncthreads();
-    for (uint32_t g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
-        const uint32_t c = g * kGroupChunks + warp;
-        if (c >= a.n_chunks) continue;
+    const uint32_t parts = a.parts ? a.parts : 1u, span = (uint32_t)kChunkTiles / parts;
+    const uint32_t units = a.n_chunks * parts;
+    for (uint32_t u = blockIdx.x * kLookupWarps + warp; u < units; u += gridDim.x * kLookupWarps) {
+        const uint32_t c = u / parts, p = u % parts;
+        const uint32_t g = c / kGroupChunks, k = c % kGroupChunks;
         // chunk offset: group offset + counts of the earlier chunks of the group
-        const uint32_t cc = lane < warp ? __ldg(a.chunk_cnt + g * kGroupChunks + lane) : 0u;
+        const uint32_t cc = lane < k ? __ldg(a.chunk_cnt + g * kGroupChunks + lane) : 0u;
         const uint64_t base = a.group_off[g] + warp_sum(cc);
-        gather_chunk<LAYOUT, CODES, KMAX>(a, c, base, smem[warp], val1, lane);
+        gather_chunk<LAYOUT, CODES, KMAX>(a, c, base, smem[warp], val1, lane, (int)(p * span),
+                                          (int)((p + 1) * span));
     }
 }
 
@@ -164,8 +172,15 @@ void launch_gather_k(const LookK &a, cudaStream_t s) {
         }
     }
     const uint64_t resident = (uint64_t)sm_count(dev) * blocks_per_sm((const void *)fn, kLookupThreads, 0, dev);
-    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(a.n_groups, resident));
-    fn<<<grid, kLookupThreads, 0, s>>>(a);
+    // short columns: split chunks over more warps until the resident warps
+    // have about two units each or every warp holds one tile
+    LookK b = a;
+    b.parts = 1;
+    while (b.parts < (uint32_t)kChunkTiles && (uint64_t)a.n_chunks * b.parts * 2 <= resident * kLookupWarps)
+        b.parts *= 2;
+    const uint64_t ctas = ((uint64_t)a.n_chunks * b.parts + kLookupWarps - 1) / kLookupWarps;
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(ctas, resident));
+    fn<<<grid, kLookupThreads, 0, s>>>(b);
 }
 
 template <int LAYOUT, bool CODES>

@@ -87,6 +87,7 @@ struct LookK {
     uint64_t out_cap;
     uint64_t *count;
     uint32_t *status;
+    uint32_t parts;       // gather: warps sharing one chunk's tiles (1, 2, 4, 8, 16; 0 = 1)
 };
 
 
@@ -546,7 +547,8 @@ __device__ __forceinline__ void gather_dense_k4(const LookK &a, uint64_t t, uint
     __syncwarp();
 }
 
-// One warp resolves chunk c (16 tiles) whose first output slot is `base`.
+// One warp resolves tiles [tt0, tt1) of chunk c (16 tiles) whose first output
+// slot is `base` (the whole chunk by default).
 // It reads the chunk's 512 bit vector words at once. A sparse chunk (at most
 // kSparseMax selected rows) lists its rows in shared memory and resolves them
 // all in parallel across lanes; a dense chunk goes tile by tile.
@@ -554,7 +556,8 @@ __device__ __forceinline__ void gather_dense_k4(const LookK &a, uint64_t t, uint
 // registers (more registers); without it each dense tile loads its own.
 template <int LAYOUT, bool CODES, int KMAX, bool HOIST = true>
 __device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_t base, WarpSmemT<KMAX> &sm,
-                                             const int32_t *val1, uint32_t lane) {
+                                             const int32_t *val1, uint32_t lane, int tt0 = 0,
+                                             int tt1 = kChunkTiles) {
     const uint64_t nwords = (a.n + 31) / 32;
     // the chunk's words: block i (4 tiles) holds words i*128 + 4L + 0..3 at lane L
     const uint64_t w0 = (uint64_t)c * kChunkTiles * kTileWords;
@@ -574,6 +577,7 @@ __device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_
     const uint32_t chunk_total = warp_sum(cnt[0] + cnt[1] + cnt[2] + cnt[3]);
     if (chunk_total == 0) return;
     if (chunk_total <= kSparseMax) {
+        if (tt0 != 0) return;  // a sparse chunk is resolved whole, by the warp of its first tiles
         // list the selected rows (row offset inside the chunk) in row order
         uint32_t pos0 = 0;
 #pragma unroll
@@ -663,10 +667,14 @@ __device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_
             }
         }
     }
-    for (int tt = 0; tt < kChunkTiles; tt++) {
+    for (int tt = 0; tt < tt1; tt++) {
         uint32_t tc;
         if constexpr (kHoist) tc = __shfl_sync(kFull, tcl, tt);
         else tc = __shfl_sync(kFull, tcnt[tt >> 2], (tt & 3) * 8);
+        if (tt < tt0) {  // tiles of another warp of this chunk: only their slots
+            base += tc;
+            continue;
+        }
         const uint64_t t = (uint64_t)c * kChunkTiles + tt;
         if (tc && t < a.n_tiles && base < a.out_cap) {
             const uint64_t w = t * kTileWords + lane;
