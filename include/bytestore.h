@@ -209,20 +209,23 @@ uint64_t bs_lookup_workspace_bytes(const bs_column *col);
 int bs_lookup(const bs_column *col, const uint32_t *d_bits, int32_t *d_out, uint64_t out_cap,
               uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes, void *stream);
 
-/* Allocation-free lookup. The paper has no counterpart: this exists for
- * callers that cannot allocate device memory when they look up -- code running
- * inside someone else's CUDA graph construction or replay, hosts that grant a
- * fixed memory budget up front, latency-critical paths that must not reach an
- * allocator. Same arguments and results as bs_lookup, but the scratch comes from
- * a 2 MiB + 4 KiB array the library keeps in device memory (held by every GPU that
- * loads the library until the process exits); no cudaMalloc, cudaFree or other
- * allocating call is made. Columns needing more than that scratch (2 MiB +
- * 4 KiB: 2^32 rows or more; in practice none, since n < 2^32) are rejected
- * with BS_ERR_CAPACITY. The first call on a device looks up the array's device
- * address; make that first call before any stream capture. All calls share
- * the one array and it keeps the previous call's contents (each call clears
- * what it needs): calls that overlap on the GPU, from any stream or thread,
- * race and must be serialised by the caller. */
+/* Allocation-free lookup. The paper has no counterpart. It is for callers
+ * that may not allocate device memory at the moment they look up: a process
+ * that was granted a fixed device-memory budget up front and must not grow
+ * it, a latency-critical path that must never wait on an allocator, or code
+ * running where another component owns all allocation. Same arguments and
+ * results as bs_lookup, but the scratch is a 2 MiB + 4 KiB array the library
+ * keeps in device memory (held by every GPU that loads the library until the
+ * process exits); the call makes no cudaMalloc, cudaFree or other allocating
+ * call. Columns needing more scratch than that (2^32 rows or more; in
+ * practice none, since n < 2^32) are rejected with BS_ERR_CAPACITY. The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and it keeps the previous call's contents;
+ * nothing is cleared: the lookup's count kernel overwrites every scratch word
+ * the later kernels of the same call read. Calls that overlap on the GPU, from
+ * any stream or thread, race on the array and must be serialised by the
+ * caller. */
 int bs_lookup_noalloc(const bs_column *col, const uint32_t *d_bits, int32_t *d_out, uint64_t out_cap,
                       uint64_t *d_count, void *stream);
 
@@ -230,6 +233,13 @@ int bs_lookup_noalloc(const bs_column *col, const uint32_t *d_bits, int32_t *d_o
  * (PP-VBS: K bytes; ByteSlice / Bit-Packed: the k-bit code) as uint64. */
 int bs_lookup_codes(const bs_column *col, const uint32_t *d_bits, uint64_t *d_codes, uint64_t out_cap,
                     uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes, void *stream);
+
+/* Launch shape of bs_lookup's gather kernel for this column on its device
+ * (introspection for tests and tuning): *parts = warps sharing one chunk of
+ * 16 tiles (1, 2, 4, 8 or 16; short columns split chunks so that the resident
+ * warps get about two units each), *grid = CTAs launched, *resident_ctas =
+ * CTAs of that kernel resident on the whole GPU. Any pointer may be NULL. */
+int bs_lookup_shape(const bs_column *col, int32_t *parts, int32_t *grid, int32_t *resident_ctas);
 
 /* Lookup by row ids in caller order: d_out[t] = v_{d_rowids[t]}, t < m.
  * Row ids >= n set the device status word (BS_ERR_DEVICE_CHECK) and write 0. */
@@ -404,7 +414,11 @@ typedef struct {
 } bs_server_opts;
 
 typedef struct {
-    int32_t status;           /* BS_OK, or BS_ERR_NOT_READY while queued or running */
+    int32_t status;           /* BS_ERR_NOT_READY while queued or running; when done BS_OK, or why the
+                               * query failed: BS_ERR_CUDA (its batch could not be launched),
+                               * BS_ERR_DEVICE_CHECK (a bounds check failed in its batch's kernels),
+                               * BS_ERR_TIMEOUT (a bounded device wait gave up); a failed query has
+                               * count 0 and d_values NULL */
     int32_t reserved;
     uint64_t count;           /* selected rows */
     const int32_t *d_values;  /* device values, ascending row order; valid until bs_server_release */
@@ -417,6 +431,7 @@ typedef struct {
     double mean_batch;
     uint64_t result_bytes_in_use, scratch_bytes_in_use;
     uint64_t queued;
+    uint64_t failed;          /* completed queries whose status is not BS_OK */
 } bs_server_stats;
 
 typedef struct bs_server bs_server; /* opaque */
@@ -436,7 +451,8 @@ int bs_server_create(const bs_server_opts *opts, bs_server **out);
  * (the query can never fit the server's memory budgets). */
 int bs_server_submit(bs_server *s, const bs_query *q, uint64_t *ticket);
 
-/* Result of a ticket: BS_ERR_NOT_READY until it completes. */
+/* Result of a ticket: BS_ERR_NOT_READY until it completes, then the query's
+ * own status (also in res->status): BS_OK or the error that failed it. */
 int bs_server_poll(bs_server *s, uint64_t ticket, bs_query_result *res);
 
 /* Wait at most timeout_ms for a ticket (BS_ERR_TIMEOUT after that). */
@@ -452,6 +468,11 @@ int bs_server_copy_result(bs_server *s, uint64_t ticket, int32_t *dst, uint64_t 
 int bs_server_release(bs_server *s, uint64_t ticket);
 
 int bs_server_get_stats(const bs_server *s, bs_server_stats *st);
+
+/* Test hook (the paper has no counterpart): the next n batch launches of this
+ * server fail on the host with BS_ERR_CUDA before anything is enqueued, as a
+ * refused launch would; their queries complete with that status. */
+int bs_server_fail_next_launches(bs_server *s, int32_t n);
 
 /* Stops the dispatcher after the batches in flight finish, frees everything. */
 void bs_server_destroy(bs_server *s);

@@ -81,7 +81,7 @@ class bs_query_result(ctypes.Structure):
 class bs_server_stats(ctypes.Structure):
     _fields_ = [("submitted", _u64), ("completed", _u64), ("rejected", _u64), ("batches", _u64),
                 ("mean_batch", ctypes.c_double), ("result_bytes_in_use", _u64), ("scratch_bytes_in_use", _u64),
-                ("queued", _u64)]
+                ("queued", _u64), ("failed", _u64)]
 
 
 class bs_advice(ctypes.Structure):
@@ -106,6 +106,7 @@ _SIGS = {
     "bs_lookup_codes": ([_vp, _vp, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "bs_lookup_noalloc": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
     "bs_lookup_rowids": ([_vp, _vp, _u64, _vp, _vp], _i32),
+    "bs_lookup_shape": ([_vp, _vp, _vp, _vp], _i32),
     "bs_advise_layout": ([_vp, _u64, _i32, _vp, _vp], _i32),
     "bs_advise_layout_range": ([_vp, _u64, _i32, _vp, ctypes.c_double, ctypes.c_double, _vp], _i32),
     "bs_selftest_bounded_wait": ([ctypes.c_uint32, _vp], _i32),
@@ -127,6 +128,7 @@ _SIGS = {
     "bs_server_copy_result": ([_vp, _u64, _vp, _u64, _vp, _vp], _i32),
     "bs_server_get_stats": ([_vp, _vp], _i32),
     "bs_server_destroy": ([_vp], None),
+    "bs_server_fail_next_launches": ([_vp, _i32], _i32),
     "bs_strerror": ([_i32], ctypes.c_char_p),
     "bs_last_device_error": ([], _i32),
     "bs_version": ([], ctypes.c_char_p),
@@ -381,6 +383,14 @@ def bs_lookup_noalloc(col: Column, bits, out=None, out_cap: int | None = None, c
     return out, count
 
 
+def bs_lookup_shape(col: Column) -> dict:
+    """Launch shape of bs_lookup's gather kernel for this column: parts (warps
+    per 16-tile chunk), grid, resident_ctas."""
+    p, g, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().bs_lookup_shape(col.handle, ctypes.byref(p), ctypes.byref(g), ctypes.byref(r)), "bs_lookup_shape")
+    return {"parts": p.value, "grid": g.value, "resident_ctas": r.value}
+
+
 def bs_lookup_codes(col: Column, bits, out=None, out_cap: int | None = None, count=None, workspace=None,
                     stream=None):
     import torch
@@ -550,17 +560,28 @@ class Server:
                 "latency_us": r.latency_us}
 
     def poll(self, ticket: int):
+        """None while the query runs; then a dict whose 'status' is the
+        query's own (BS_OK or the error that failed it)."""
         r = bs_query_result()
         rc = lib().bs_server_poll(self.handle, ticket, ctypes.byref(r))
         if rc == BS_ERR_NOT_READY:
             return None
+        if rc != BS_OK and rc == r.status:
+            return self._res(r)  # the query finished with an error of its own
         _check(rc, "bs_server_poll")
         return self._res(r)
 
     def wait(self, ticket: int, timeout_ms: int = 60000) -> dict:
         r = bs_query_result()
-        _check(lib().bs_server_wait(self.handle, ticket, int(timeout_ms), ctypes.byref(r)), "bs_server_wait")
+        rc = lib().bs_server_wait(self.handle, ticket, int(timeout_ms), ctypes.byref(r))
+        if rc != BS_OK and rc == r.status:
+            return self._res(r)  # the query finished with an error of its own
+        _check(rc, "bs_server_wait")
         return self._res(r)
+
+    def fail_next_launches(self, n: int):
+        """Test hook: the next n batch launches fail on the host (BS_ERR_CUDA)."""
+        _check(lib().bs_server_fail_next_launches(self.handle, int(n)), "bs_server_fail_next_launches")
 
     def values(self, ticket: int, count: int, stream=None):
         """Copy a finished query's values into a new CUDA int32 tensor."""

@@ -331,6 +331,7 @@ struct PlainReq {
     uint64_t *count;
     uint32_t *bits;  // scratch: result bit vector
     void *ws;        // scratch: lookup workspace
+    uint32_t *status;  // device word the kernels report bounds / timeout flags into
 };
 
 // Validates request q and fills R's predicate and lookup fields and P
@@ -404,16 +405,17 @@ void bind_scratch(BReq &R, PlainReq &P, uint8_t *p, uint32_t *user_bits, uint32_
     for (int q = 0; q < R.npred; q++) R.pred[q].a.status = status;
     P.bits = R.bits;
     P.ws = R.chunk_cnt;
+    P.status = status;
 }
 
 // The single-query kernels of one request: the conjunction's scans (each after
 // the first seeded by, and overwriting, the running bit vector), then the lookup.
 int launch_plain(const PlainReq &P, cudaStream_t s) {
     for (int p = 0; p < P.npred; p++) {
-        const int rc = launch_scan(*P.col[p], P.kp[p], p ? P.bits : nullptr, P.bits, s);
+        const int rc = launch_scan(*P.col[p], P.kp[p], p ? P.bits : nullptr, P.bits, s, P.status);
         if (rc) return rc;
     }
-    return launch_lookup(*P.proj, P.bits, P.out, nullptr, P.cap, P.count, P.ws, s);
+    return launch_lookup(*P.proj, P.bits, P.out, nullptr, P.cap, P.count, P.ws, s, P.status);
 }
 
 // ------------------------------------------------------------- tuning cache
@@ -788,6 +790,7 @@ struct QueryRec {
     size_t out_bytes = 0, out_off = SIZE_MAX;
     size_t scratch_bytes = 0, scratch_off = SIZE_MAX;
     int state = 0;                // 0 queued, 1 running, 2 done
+    int rc = 0;                   // BS_OK, or why the query failed (launch error, device check, timeout)
     uint64_t count = 0;
     Clock::time_point t_submit, t_launch, t_done;
 };
@@ -795,9 +798,9 @@ struct QueryRec {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    uint8_t *d_desc = nullptr;    // BReq[max_batch] | unit0 | seg0 | ctr + segment totals | counts
+    uint8_t *d_desc = nullptr;    // BReq[max_batch] | unit0 | seg0 | ctr + segment totals | counts | status
     uint8_t *h_desc = nullptr;    // pinned mirror
-    size_t desc_bytes = 0, o_unit0 = 0, o_seg0 = 0, o_ctr = 0, o_counts = 0;
+    size_t desc_bytes = 0, o_unit0 = 0, o_seg0 = 0, o_ctr = 0, o_counts = 0, o_status = 0;
     std::vector<bs::PlainReq> plain;  // this batch's queries for the single-query kernels
     bool busy = false;
     std::vector<uint64_t> tickets;
@@ -820,6 +823,7 @@ struct bs_server {
     uint64_t next_ticket = 1;
     bs_server_stats stats{};
     uint64_t batched_queries = 0;
+    int fail_launches = 0;        // test hook: batch launches still to fail on the host
     bool stop = false;
     std::thread th;
 };
@@ -832,6 +836,13 @@ namespace {
 // pinned mirror), then the read-back of all counts and the completion event.
 int launch_slot(bs_server *S, Slot &sl, int nall, int nreq, uint32_t total_units, uint32_t total_segs) {
     using namespace bs;
+    if (S->fail_launches > 0) {  // a launch failure faked on the host, before anything is enqueued
+        S->fail_launches--;
+        return BS_ERR_CUDA;
+    }
+    // the slot's own status word collects its kernels' bounds and timeout flags
+    uint32_t *st = (uint32_t *)(sl.d_desc + sl.o_status);
+    if (cudaMemsetAsync(st, 0, 8, sl.stream) != cudaSuccess) return BS_ERR_CUDA;
     for (const PlainReq &P : sl.plain) {
         const int rc = launch_plain(P, sl.stream);
         if (rc) return rc;
@@ -845,7 +856,7 @@ int launch_slot(bs_server *S, Slot &sl, int nall, int nreq, uint32_t total_units
         k.total_units = total_units;
         k.total_segs = total_segs;
         k.ctr = (uint32_t *)(sl.d_desc + sl.o_ctr);
-        k.status = S->status;
+        k.status = st;
         if (cudaMemcpyAsync(sl.d_desc, sl.h_desc, sl.o_ctr, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
             return BS_ERR_CUDA;
         if (cudaMemsetAsync(k.ctr, 0, 256 + (size_t)total_segs * 8, sl.stream) != cudaSuccess) return BS_ERR_CUDA;
@@ -861,8 +872,9 @@ int launch_slot(bs_server *S, Slot &sl, int nall, int nreq, uint32_t total_units
         cfg.numAttrs = 1;
         if (cudaLaunchKernelEx(&cfg, batch_kernel, k) != cudaSuccess) return BS_ERR_CUDA;
     }
-    if (cudaMemcpyAsync(sl.h_desc + sl.o_counts, sl.d_desc + sl.o_counts, (size_t)nall * 8, cudaMemcpyDeviceToHost,
-                        sl.stream) != cudaSuccess)
+    // counts and the status word in one copy (the status word follows the counts)
+    if (cudaMemcpyAsync(sl.h_desc + sl.o_counts, sl.d_desc + sl.o_counts, sl.o_status + 8 - sl.o_counts,
+                        cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
         return BS_ERR_CUDA;
     if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return BS_ERR_CUDA;
     return BS_OK;
@@ -879,14 +891,20 @@ void dispatcher(bs_server *S) {
             if (!sl.busy || cudaEventQuery(sl.done) != cudaSuccess) continue;
             const auto now = Clock::now();
             const uint64_t *counts = (const uint64_t *)(sl.h_desc + sl.o_counts);
+            // a bounds check or a bounded wait that failed in this batch's kernels
+            // fails every query of the batch (their results cannot be trusted)
+            const uint32_t dev_st = *(const uint32_t *)(sl.h_desc + sl.o_status);
+            const int brc = (dev_st & kStatusTimeout) ? BS_ERR_TIMEOUT : (dev_st ? BS_ERR_DEVICE_CHECK : BS_OK);
             for (size_t i = 0; i < sl.tickets.size(); i++) {
                 QueryRec &q = S->recs[sl.tickets[i]];
-                q.count = counts[i];
+                q.count = brc == BS_OK ? counts[i] : 0;
+                q.rc = brc;
                 q.t_done = now;
                 q.state = 2;
                 S->scratch_alloc.release(q.scratch_off, q.scratch_bytes);
                 q.scratch_off = SIZE_MAX;
                 S->stats.completed++;
+                if (brc != BS_OK) S->stats.failed++;
             }
             sl.tickets.clear();
             sl.busy = false;
@@ -921,7 +939,7 @@ void dispatcher(bs_server *S) {
                 R.look.out_vals = (int32_t *)(S->d_result + ro);
                 R.look.out_cap = q.bound;
                 R.look.count = d_counts + nb;
-                bind_scratch(R, P, S->d_scratch + so, nullptr, S->status);
+                bind_scratch(R, P, S->d_scratch + so, nullptr, (uint32_t *)(sl.d_desc + sl.o_status));
                 P.out = R.look.out_vals;
                 P.cap = q.bound;
                 P.count = R.look.count;
@@ -947,14 +965,25 @@ void dispatcher(bs_server *S) {
             seg0[nk] = segs;
             const auto now = Clock::now();
             for (uint64_t tk : sl.tickets) S->recs[tk].t_launch = now;
-            if (launch_slot(S, sl, nb, nk, units, segs) != BS_OK) {
-                // record the failure on the queries; they complete with count 0
+            const int lrc = launch_slot(S, sl, nb, nk, units, segs);
+            if (lrc != BS_OK) {
+                // whatever part of the batch was enqueued finishes before its
+                // memory is handed out again; the queries complete with the
+                // launch error as their status and no result
+                cudaStreamSynchronize(sl.stream);
+                cudaGetLastError();
                 for (uint64_t tk : sl.tickets) {
                     QueryRec &q = S->recs[tk];
                     q.state = 2;
+                    q.rc = lrc;
+                    q.count = 0;
                     q.t_done = Clock::now();
                     S->scratch_alloc.release(q.scratch_off, q.scratch_bytes);
                     q.scratch_off = SIZE_MAX;
+                    S->result_alloc.release(q.out_off, q.out_bytes);
+                    q.out_off = SIZE_MAX;
+                    S->stats.completed++;
+                    S->stats.failed++;
                 }
                 sl.tickets.clear();
                 S->cv_done.notify_all();
@@ -1061,6 +1090,8 @@ int bs_server_create(const bs_server_opts *opts, bs_server **out) {
         // counters, then up to 512 segment totals per query (n < 2^32 rows)
         sl.o_ctr = take(256 + (size_t)o.max_batch * 512 * 8);
         sl.o_counts = take((size_t)o.max_batch * 8);
+        sl.o_status = sl.o_counts + (size_t)o.max_batch * 8;  // right after the counts (8-byte aligned)
+        at = sl.o_status + 8;
         sl.desc_bytes = at;
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
@@ -1116,18 +1147,21 @@ int bs_server_submit(bs_server *S, const bs_query *q, uint64_t *ticket) {
     return BS_OK;
 }
 
+// A finished query reports its own status both in res->status and as the
+// return value: BS_OK, or the launch error / device check / timeout that
+// failed it (then count is 0 and d_values NULL).
 static int fill_result(bs_server *S, const QueryRec &q, bs_query_result *res) {
     std::memset(res, 0, sizeof *res);
     if (q.state != 2) {
         res->status = BS_ERR_NOT_READY;
         return BS_ERR_NOT_READY;
     }
-    res->status = BS_OK;
+    res->status = q.rc;
     res->count = q.count;
-    res->d_values = q.out_off == SIZE_MAX ? nullptr : (const int32_t *)(S->d_result + q.out_off);
+    res->d_values = (q.rc != BS_OK || q.out_off == SIZE_MAX) ? nullptr : (const int32_t *)(S->d_result + q.out_off);
     res->queue_us = us_since(q.t_submit, q.t_launch);
     res->latency_us = us_since(q.t_submit, q.t_done);
-    return BS_OK;
+    return q.rc;
 }
 
 int bs_server_poll(bs_server *S, uint64_t ticket, bs_query_result *res) {
@@ -1163,6 +1197,7 @@ int bs_server_copy_result(bs_server *S, uint64_t ticket, int32_t *dst, uint64_t 
         auto it = S->recs.find(ticket);
         if (it == S->recs.end()) return BS_ERR_INVALID_ARG;
         if (it->second.state != 2) return BS_ERR_NOT_READY;
+        if (it->second.rc != BS_OK) return it->second.rc;
         if (it->second.out_off == SIZE_MAX) return BS_ERR_INVALID_ARG;
         src = (const int32_t *)(S->d_result + it->second.out_off);
         n = std::min(cap, it->second.count);
@@ -1196,6 +1231,13 @@ int bs_server_get_stats(const bs_server *S, bs_server_stats *st) {
     st->result_bytes_in_use = S->result_alloc.used();
     st->scratch_bytes_in_use = S->scratch_alloc.used();
     st->queued = S->queue.size();
+    return BS_OK;
+}
+
+int bs_server_fail_next_launches(bs_server *S, int32_t n) {
+    if (!S || n < 0) return BS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(S->mu);
+    S->fail_launches = n;
     return BS_OK;
 }
 

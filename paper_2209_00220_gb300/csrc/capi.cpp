@@ -294,6 +294,19 @@ int bs_lookup_codes(const bs_column *col, const uint32_t *d_bits, uint64_t *d_co
                          workspace_bytes, stream);
 }
 
+int bs_lookup_shape(const bs_column *col, int32_t *parts, int32_t *grid, int32_t *resident_ctas) {
+    if (!col) return BS_ERR_INVALID_ARG;
+    if (!on_device(col)) return BS_ERR_UNSUPPORTED;
+    DeviceGuard g(col->c.device);
+    if (!g.ok) return BS_ERR_CUDA;
+    uint32_t p = 0, gr = 0, r = 0;
+    const int rc = bs::lookup_shape(col->c, &p, &gr, &r);
+    if (parts) *parts = (int32_t)p;
+    if (grid) *grid = (int32_t)gr;
+    if (resident_ctas) *resident_ctas = (int32_t)r;
+    return rc;
+}
+
 int bs_lookup_rowids(const bs_column *col, const uint32_t *d_rowids, uint64_t m, int32_t *d_out, void *stream) {
     if (!col || (m && (!d_rowids || !d_out))) return BS_ERR_INVALID_ARG;
     if (col->c.raw || !on_device(col)) return BS_ERR_UNSUPPORTED;

@@ -12,12 +12,18 @@ namespace bs {
 constexpr uint32_t kStatusBounds = 1u;   // an index failed its bounds check
 constexpr uint32_t kStatusTimeout = 2u;  // a bounded wait gave up
 
-int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_t *d_out, cudaStream_t s);
+// status: device word the kernels report bounds / timeout flags into (NULL:
+// the library's status word of the current device).
+int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_t *d_out, cudaStream_t s,
+                uint32_t *status = nullptr);
 
 uint64_t lookup_workspace_bytes(const Column &c);
 // Either d_vals or d_codes is non-null.
 int launch_lookup(const Column &c, const uint32_t *d_bits, int32_t *d_vals, uint64_t *d_codes, uint64_t out_cap,
-                  uint64_t *d_count, void *d_ws, cudaStream_t s);
+                  uint64_t *d_count, void *d_ws, cudaStream_t s, uint32_t *status = nullptr);
+// Launch shape bs_lookup's gather kernel takes for this column (values, not
+// codes): warps per 16-tile chunk, grid, resident CTAs (current device).
+int lookup_shape(const Column &c, uint32_t *parts, uint32_t *grid, uint32_t *resident);
 int launch_lookup_rowids(const Column &c, const uint32_t *d_rowids, uint64_t m, int32_t *d_out, cudaStream_t s);
 
 int read_and_clear_status(uint32_t *status);

@@ -12,6 +12,12 @@ namespace bs {
 namespace {
 
 // ------------------------------------------------------------ 1. count
+// Writes chunk_cnt[c] for every chunk c < n_chunks and group_off[g] for every
+// group g < n_groups (one CTA per group), whatever the bits hold: the scan and
+// gather kernels read nothing of the workspace that this kernel did not write
+// in the same call, so the workspace is never cleared (bs_lookup_noalloc's
+// shared scratch relies on this; a count kernel that skipped empty chunks
+// would break it).
 __global__ void __launch_bounds__(kLookupThreads) lookup_count_kernel(const LookK a) {
     __shared__ uint32_t part[kLookupWarps];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -150,10 +156,16 @@ __global__ void lookup_rowids_kernel(const LookK a, const uint32_t *rowids, uint
     }
 }
 
+// Launch shape of the gather for a column: warps per chunk (parts), grid and
+// the resident CTAs the grid is capped at. Short columns split chunks over
+// more warps until the resident warps have about two units each or every warp
+// holds one tile.
+struct GatherShape {
+    uint32_t parts, grid, resident;
+};
+
 template <int LAYOUT, bool CODES, int KMAX>
-void launch_gather_k(const LookK &a, cudaStream_t s) {
-    int dev = 0;
-    cudaGetDevice(&dev);
+GatherShape gather_shape_k(const LookK &a, int dev) {
     auto fn = lookup_gather_kernel<LAYOUT, CODES, KMAX>;
     if (KMAX > 2) {
         // codes of three or more bytes read BS_3.., the leaf table and the
@@ -171,16 +183,32 @@ void launch_gather_k(const LookK &a, cudaStream_t s) {
             done.fetch_or(bit);
         }
     }
+    GatherShape g;
     const uint64_t resident = (uint64_t)sm_count(dev) * blocks_per_sm((const void *)fn, kLookupThreads, 0, dev);
-    // short columns: split chunks over more warps until the resident warps
-    // have about two units each or every warp holds one tile
+    g.resident = (uint32_t)resident;
+    g.parts = 1;
+    while (g.parts < (uint32_t)kChunkTiles && (uint64_t)a.n_chunks * g.parts * 2 <= resident * kLookupWarps)
+        g.parts *= 2;
+    const uint64_t ctas = ((uint64_t)a.n_chunks * g.parts + kLookupWarps - 1) / kLookupWarps;
+    g.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(ctas, resident));
+    return g;
+}
+
+template <int LAYOUT, bool CODES, int KMAX>
+void launch_gather_k(const LookK &a, cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const GatherShape g = gather_shape_k<LAYOUT, CODES, KMAX>(a, dev);
     LookK b = a;
-    b.parts = 1;
-    while (b.parts < (uint32_t)kChunkTiles && (uint64_t)a.n_chunks * b.parts * 2 <= resident * kLookupWarps)
-        b.parts *= 2;
-    const uint64_t ctas = ((uint64_t)a.n_chunks * b.parts + kLookupWarps - 1) / kLookupWarps;
-    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(ctas, resident));
-    fn<<<grid, kLookupThreads, 0, s>>>(b);
+    b.parts = g.parts;
+    lookup_gather_kernel<LAYOUT, CODES, KMAX><<<g.grid, kLookupThreads, 0, s>>>(b);
+}
+
+template <int LAYOUT>
+GatherShape gather_shape(const LookK &a, int dev) {
+    if (LAYOUT == BS_PPVBS && a.K > 4) return gather_shape_k<LAYOUT, false, 8>(a, dev);
+    if (a.K > 2) return gather_shape_k<LAYOUT, false, 4>(a, dev);
+    return gather_shape_k<LAYOUT, false, 2>(a, dev);
 }
 
 template <int LAYOUT, bool CODES>
@@ -203,6 +231,22 @@ void launch_kernels(const LookK &a, cudaStream_t s) {
 
 }  // namespace
 
+int lookup_shape(const Column &c, uint32_t *parts, uint32_t *grid, uint32_t *resident) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BS_ERR_CUDA;
+    const LookK a = make_look_args(c);
+    GatherShape g;
+    switch (c.layout) {
+    case BS_PPVBS: g = gather_shape<BS_PPVBS>(a, dev); break;
+    case BS_BYTESLICE: g = gather_shape<BS_BYTESLICE>(a, dev); break;
+    default: g = gather_shape<BS_BITPACKED>(a, dev); break;
+    }
+    if (parts) *parts = g.parts;
+    if (grid) *grid = g.grid;
+    if (resident) *resident = g.resident;
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ERR_CUDA;
+}
+
 uint64_t lookup_workspace_bytes(const Column &c) {
     const uint64_t chunks = ((uint64_t)c.n_tiles + kChunkTiles - 1) / kChunkTiles;
     const uint64_t groups = (chunks + kGroupChunks - 1) / kGroupChunks;
@@ -210,7 +254,7 @@ uint64_t lookup_workspace_bytes(const Column &c) {
 }
 
 int launch_lookup(const Column &c, const uint32_t *d_bits, int32_t *d_vals, uint64_t *d_codes, uint64_t out_cap,
-                  uint64_t *d_count, void *d_ws, cudaStream_t s) {
+                  uint64_t *d_count, void *d_ws, cudaStream_t s, uint32_t *status) {
     LookK a = make_look_args(c);
     a.bits = d_bits;
     a.bits_vec = ((uintptr_t)d_bits & 15u) == 0;
@@ -220,7 +264,7 @@ int launch_lookup(const Column &c, const uint32_t *d_bits, int32_t *d_vals, uint
     a.out_codes = d_codes;
     a.out_cap = out_cap;
     a.count = d_count;
-    a.status = status_word();
+    a.status = status ? status : status_word();
     if (!a.status) return BS_ERR_CUDA;
     if (c.n == 0) {
         if (d_count && cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s) != cudaSuccess) return BS_ERR_CUDA;

@@ -178,7 +178,8 @@ KernelFn packed_kernel_for(int k) { return packed_table(k, std::make_integer_seq
 
 }  // namespace
 
-int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_t *d_out, cudaStream_t s) {
+int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_t *d_out, cudaStream_t s,
+                uint32_t *status) {
     if (c.n == 0) return BS_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return BS_ERR_CUDA;
@@ -186,7 +187,7 @@ int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_
     ScanPlan plan{};
     plan_scan(c, p, d_seed, true, a, plan);
     a.out = d_out;
-    a.status = status_word();
+    a.status = status ? status : status_word();
     if (!a.status) return BS_ERR_CUDA;
     if (plan.kind == ScanPlan::kFill) {
         const uint64_t nwords = (c.n + 31) / 32;

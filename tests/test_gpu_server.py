@@ -99,3 +99,31 @@ def test_server_admission_by_memory(B):
         B.bs_server_create(max_batch=4, result_bytes=1024).submit([(cols[0], "lt", a)])
     srv.destroy()
     assert B.bs_last_device_error() == 0
+
+
+def test_server_reports_failed_launch_per_query(B):
+    """A batch whose launch fails (faked on the host, before anything is
+    enqueued) completes its queries with that error as their own status, no
+    count and no values, and frees their memory; the next queries run normally."""
+    vals, cols = _table(B, 300007, 41, k=1)
+    v = vals[0]
+    a, _ = synth.pick_literals(v, "lt", 0.2, 0)
+    want = v[v < a]
+    srv = B.bs_server_create(max_batch=4, slots=1, result_bytes=64 << 20, scratch_bytes=256 << 20)
+    srv.fail_next_launches(1)
+    t_bad = srv.submit([(cols[0], "lt", a)])
+    r = srv.wait(t_bad, 60000)
+    assert r["status"] == B.BS_ERR_CUDA and r["count"] == 0 and not r["d_values"]
+    with pytest.raises(B.BsError):
+        srv.values(t_bad, 1)
+    st = srv.stats()
+    assert st["failed"] == 1 and st["result_bytes_in_use"] == 0 and st["scratch_bytes_in_use"] == 0
+    srv.release(t_bad)
+    t_ok = srv.submit([(cols[0], "lt", a)])
+    r = srv.wait(t_ok, 60000)
+    assert r["status"] == 0 and r["count"] == want.size
+    assert np.array_equal(srv.values(t_ok, r["count"]).cpu().numpy(), want)
+    srv.release(t_ok)
+    assert srv.stats()["failed"] == 1
+    srv.destroy()
+    assert B.bs_last_device_error() == 0
