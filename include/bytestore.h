@@ -234,6 +234,33 @@ int bs_lookup_noalloc(const bs_column *col, const uint32_t *d_bits, int32_t *d_o
 int bs_lookup_codes(const bs_column *col, const uint32_t *d_bits, uint64_t *d_codes, uint64_t out_cap,
                     uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------- fused scan + lookup */
+
+/* Device workspace bytes bs_scan_lookup needs for a projection column of this
+ * length (8 bytes per 2048 rows plus 256). */
+uint64_t bs_scan_lookup_workspace_bytes(const bs_column *proj);
+
+/* Fused scan + lookup (Section 2.2's query shape: a conjunction of predicates
+ * evaluated by pipelined bit vectors, Section 3.3.1, then the lookup of a
+ * projected column, Algorithm 4) in one kernel: the values of `proj` at the
+ * rows where every predicate holds, in ascending row order, written to d_out
+ * (device int32, out_cap entries; only the first out_cap values are written),
+ * and the number of such rows to *d_count (device uint64, may be NULL) even
+ * when it exceeds out_cap. The same results as bs_scan_conj followed by
+ * bs_lookup, without the bit vector's round trip through memory and without
+ * the lookup's separate count and offset kernels: each pair of tiles finds
+ * its output offset from the counts of the earlier ones (decoupled look-back).
+ * preds: 1..BS_MAX_CONJ predicates over columns of proj's length on proj's
+ * device; proj NULL = preds[0].col. d_bits: NULL, or ceil(n/32) device words
+ * that also receive the result bit vector (bits >= n zero). d_workspace:
+ * device scratch of bs_scan_lookup_workspace_bytes(proj) bytes (cleared by
+ * the call, stream-ordered), or NULL to let the call allocate and free it.
+ * Errors: INVALID_ARG, UNSUPPORTED (raw-code or host-only columns, categorical
+ * columns with an order predicate), CAPACITY (workspace too small), OOM, CUDA;
+ * a look-back that gives up records BS_ERR_TIMEOUT for bs_last_device_error. */
+int bs_scan_lookup(const bs_pred *preds, int32_t npreds, const bs_column *proj, uint32_t *d_bits, int32_t *d_out,
+                   uint64_t out_cap, uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes, void *stream);
+
 /* Launch shape of bs_lookup's gather kernel for this column on its device
  * (introspection for tests and tuning): *parts = warps sharing one chunk of
  * 16 tiles (1, 2, 4, 8 or 16; short columns split chunks so that the resident
@@ -293,6 +320,18 @@ typedef struct {
 } bs_lookup_bytes_t;
 
 int bs_lookup_bytes(const bs_column *col, const uint32_t *h_bits, bs_lookup_bytes_t *out);
+
+/* Bytes the fused scan + lookup (bs_scan_lookup) must move for one predicate
+ * projected onto its own column: the scan's sectors as bs_scan_bytes counts
+ * them, plus, for every row selected (h_sel: the predicate's result bit
+ * vector, host memory), the sectors of the rest of its code with the M_j
+ * sector and off_j entry of each level it reaches; each sector counted once.
+ * result_bytes = 4 bytes per selected row (the values written) plus the bit
+ * vector when write_bits != 0. Needs the host copy of the layout. PP-VBS and
+ * Bit-Packed columns (a Bit-Packed scan already reads every code); ByteSlice:
+ * BS_ERR_UNSUPPORTED. */
+int bs_scan_lookup_bytes(const bs_column *col, bs_op op, int32_t lit, int32_t lit2, const uint32_t *h_sel,
+                         int32_t write_bits, bs_scan_bytes_t *out);
 
 /* ---------------------------------------------------- layout advisor */
 

@@ -107,6 +107,8 @@ _SIGS = {
     "bs_lookup_noalloc": ([_vp, _vp, _vp, _u64, _vp, _vp], _i32),
     "bs_lookup_rowids": ([_vp, _vp, _u64, _vp, _vp], _i32),
     "bs_lookup_shape": ([_vp, _vp, _vp, _vp], _i32),
+    "bs_scan_lookup_workspace_bytes": ([_vp], _u64),
+    "bs_scan_lookup": ([_vp, _i32, _vp, _vp, _vp, _u64, _vp, _vp, _u64, _vp], _i32),
     "bs_advise_layout": ([_vp, _u64, _i32, _vp, _vp], _i32),
     "bs_advise_layout_range": ([_vp, _u64, _i32, _vp, ctypes.c_double, ctypes.c_double, _vp], _i32),
     "bs_selftest_bounded_wait": ([ctypes.c_uint32, _vp], _i32),
@@ -114,6 +116,7 @@ _SIGS = {
     "bs_column_load": ([ctypes.c_char_p, _vp, _vp], _i32),
     "bs_scan_bytes": ([_vp, _i32, _i32, _i32, _vp, _vp], _i32),
     "bs_lookup_bytes": ([_vp, _vp, _vp], _i32),
+    "bs_scan_lookup_bytes": ([_vp, _i32, _i32, _i32, _vp, _i32, _vp], _i32),
     "bs_scan_bytes_sampled": ([_vp, _i32, _i32, _i32, _vp, _u64, _vp], _i32),
     "bs_batch_create": ([_vp, _i32, _vp, _vp], _i32),
     "bs_batch_launch": ([_vp, _vp], _i32),
@@ -383,6 +386,37 @@ def bs_lookup_noalloc(col: Column, bits, out=None, out_cap: int | None = None, c
     return out, count
 
 
+def bs_scan_lookup_workspace_bytes(proj: Column) -> int:
+    return int(lib().bs_scan_lookup_workspace_bytes(proj.handle))
+
+
+def bs_scan_lookup(preds, proj: Column | None = None, out=None, out_cap: int | None = None, count=None,
+                   bits=None, workspace=None, stream=None):
+    """Fused conjunction + lookup: preds [(Column, op, lit[, lit2]), ...] (1..4),
+    then the values of proj (default: the first predicate's column) at the
+    selected rows. bits: optional int32 tensor of ceil(n/32) words that also
+    receives the result bit vector. Returns (values tensor, count tensor)."""
+    import torch
+    if not 1 <= len(preds) <= 4:
+        raise BsError(BS_ERR_INVALID_ARG, "bs_scan_lookup: 1..4 predicates")
+    arr = (bs_pred * len(preds))()
+    for i, p in enumerate(preds):
+        arr[i].col = p[0].handle
+        arr[i].op = OPS[p[1]]
+        arr[i].lit = int(p[2])
+        arr[i].lit2 = int(p[3]) if len(p) > 3 else 0
+    pc = proj if proj is not None else preds[0][0]
+    if out is None:
+        out = torch.empty(max(1, pc.n if out_cap is None else out_cap), dtype=torch.int32, device="cuda")
+    cap = out.numel() if out_cap is None else int(out_cap)
+    if count is None:
+        count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(lib().bs_scan_lookup(arr, len(preds), pc.handle, _dptr(bits), _dptr(out), cap, _dptr(count),
+                                _dptr(workspace), ws_bytes, _stream(stream)), "bs_scan_lookup")
+    return out, count
+
+
 def bs_lookup_shape(col: Column) -> dict:
     """Launch shape of bs_lookup's gather kernel for this column: parts (warps
     per 16-tile chunk), grid, resident_ctas."""
@@ -444,6 +478,16 @@ def bs_lookup_bytes(col: Column, bits) -> dict:
     b = _np(bits, np.uint32)
     _check(lib().bs_lookup_bytes(col.handle, b.ctypes.data if b.size else None, ctypes.byref(r)),
            "bs_lookup_bytes")
+    return _struct_dict(r)
+
+
+def bs_scan_lookup_bytes(col: Column, op: str, lit: int, lit2: int, sel, write_bits: bool = True) -> dict:
+    """Bytes the fused scan + lookup must move for one predicate projected onto
+    its own column; sel: host numpy uint32 result bit vector."""
+    r = bs_scan_bytes_t()
+    b = _np(sel, np.uint32)
+    _check(lib().bs_scan_lookup_bytes(col.handle, OPS[op], int(lit), int(lit2), b.ctypes.data if b.size else None,
+                                      1 if write_bits else 0, ctypes.byref(r)), "bs_scan_lookup_bytes")
     return _struct_dict(r)
 
 

@@ -61,6 +61,15 @@ int bs_scan_bytes_sampled(const bs_column *col, bs_op op, int32_t lit, int32_t l
     return bs::scan_bytes(col->c, p, h_seed, tile_stride, out);
 }
 
+int bs_scan_lookup_bytes(const bs_column *col, bs_op op, int32_t lit, int32_t lit2, const uint32_t *h_sel,
+                         int32_t write_bits, bs_scan_bytes_t *out) {
+    if (!col || !out || op < BS_LT || op > BS_BETWEEN || (col->c.n && !h_sel)) return BS_ERR_INVALID_ARG;
+    bs::KPred p;
+    int rc = bs::rewrite_literal(col->c, op, lit, lit2, p);
+    if (rc) return rc;
+    return bs::scan_lookup_bytes(col->c, p, h_sel, write_bits != 0, out);
+}
+
 int bs_lookup_bytes(const bs_column *col, const uint32_t *h_bits, bs_lookup_bytes_t *out) {
     if (!col || !out || (col->c.n && !h_bits)) return BS_ERR_INVALID_ARG;
     return bs::lookup_bytes(col->c, h_bits, out);

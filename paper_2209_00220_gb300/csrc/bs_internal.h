@@ -124,6 +124,7 @@ uint64_t estimate_rows(const Column &c, int op, int32_t lit, int32_t lit2);
 // tile_stride-th tile and scales up
 int scan_bytes(const Column &c, const KPred &p, const uint32_t *seed, uint64_t tile_stride, bs_scan_bytes_t *out);
 int lookup_bytes(const Column &c, const uint32_t *bits, bs_lookup_bytes_t *out);
+int scan_lookup_bytes(const Column &c, const KPred &p, const uint32_t *sel, bool write_bits, bs_scan_bytes_t *out);
 
 // device side (column.cu)
 int upload_column(Column &c);

@@ -83,7 +83,13 @@ void replay_row(const uint8_t *code, int L, const Lit &lit, int K, bool need_eq,
 
 }  // namespace
 
-int scan_bytes(const Column &c, const KPred &p, const uint32_t *seed, uint64_t tile_stride, bs_scan_bytes_t *out) {
+// sel (fused scan + lookup on the same column): the predicate's result; the
+// rows it selects also have every byte of their code read, with the M_j sector
+// and off_j entry of each level they reach (as the lookup reads them), and 4
+// output bytes each; write_bits: the result bit vector is written (else it is
+// not counted).
+int scan_bytes_impl(const Column &c, const KPred &p, const uint32_t *seed, uint64_t tile_stride, const uint32_t *sel,
+                    bool write_bits, bs_scan_bytes_t *out) {
     std::memset(out, 0, sizeof *out);
     const uint64_t n = c.n;
     const uint64_t nwords = (n + 31) / 32;
@@ -93,8 +99,15 @@ int scan_bytes(const Column &c, const KPred &p, const uint32_t *seed, uint64_t t
     const uint64_t nt = c.n_tiles;
     const uint64_t sampled = (nt + tile_stride - 1) / tile_stride;
     const double scale = (double)nt / (double)sampled;
-    out->result_bytes = 4 * nwords + (seed ? 4 * nwords : 0);
+    uint64_t selected = 0;
+    if (sel)
+        for (uint64_t w = 0; w < nwords; w++) {
+            const uint32_t v = (w == nwords - 1 && (n & 31)) ? ((1u << (n & 31)) - 1u) : 0xFFFFFFFFu;
+            selected += (uint64_t)__builtin_popcount(sel[w] & v);
+        }
+    out->result_bytes = (write_bits ? 4 * nwords : 0) + (seed ? 4 * nwords : 0) + 4 * selected;
     if (p.mode != Pred::kNormal) {
+        if (sel && selected) return BS_ERR_UNSUPPORTED;  // constant predicates: not replayed for lookups
         out->bytes = out->result_bytes;
         out->paper_model_bytes = out->result_bytes;
         return BS_OK;
@@ -168,6 +181,7 @@ int scan_bytes(const Column &c, const KPred &p, const uint32_t *seed, uint64_t t
                 }
                 if (!on) continue;
                 lane_active[lane] = true;
+                const bool picked = sel && ((sel[w] >> (row & 31)) & 1u);
                 int pend_to = 1, byte_to = 1;
                 for (int i = 0; i < nlit; i++) {
                     int pt, bt;
@@ -191,8 +205,16 @@ int scan_bytes(const Column &c, const KPred &p, const uint32_t *seed, uint64_t t
                     grp_pend[j][g] = true;
                 }
                 block_stop[lane] = std::max(block_stop[lane], pend_to);
+                if (picked) {
+                    // the lookup of a selected row: every byte of its code
+                    for (int j = 2; j <= std::min(L + 1, K); j++) {
+                        grp_pend[j][g] = true;
+                        grp_byte[j][g] = true;
+                    }
+                }
                 if (c.layout == BS_PPVBS) {
-                    for (int j = 2; j <= byte_to; j++) {
+                    const int read_to = picked ? std::max(byte_to, L) : byte_to;
+                    for (int j = 2; j <= read_to; j++) {
                         grp_byte[j][g] = true;
                         A.deep_run[j].add(byte_addr[j]);
                     }
@@ -251,6 +273,18 @@ int scan_bytes(const Column &c, const KPred &p, const uint32_t *seed, uint64_t t
     out->paper_model_bytes = c.layout == BS_PPVBS ? (uint64_t)(paper * scale) + 4 * nwords : out->bytes;
     out->sampled_tiles = sampled;
     return BS_OK;
+}
+
+int scan_bytes(const Column &c, const KPred &p, const uint32_t *seed, uint64_t tile_stride, bs_scan_bytes_t *out) {
+    return scan_bytes_impl(c, p, seed, tile_stride, nullptr, true, out);
+}
+
+int scan_lookup_bytes(const Column &c, const KPred &p, const uint32_t *sel, bool write_bits, bs_scan_bytes_t *out) {
+    if (!sel && c.n) return BS_ERR_INVALID_ARG;
+    // ByteSlice lookups read single sectors of the deeper slices, which the
+    // scan's lane-pair accounting does not express: not counted here
+    if (c.layout == BS_BYTESLICE) return BS_ERR_UNSUPPORTED;
+    return scan_bytes_impl(c, p, nullptr, 1, sel, write_bits, out);
 }
 
 // Lookup: the bit vector once, the output values, and the distinct sectors of

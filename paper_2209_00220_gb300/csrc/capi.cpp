@@ -294,6 +294,48 @@ int bs_lookup_codes(const bs_column *col, const uint32_t *d_bits, uint64_t *d_co
                          workspace_bytes, stream);
 }
 
+uint64_t bs_scan_lookup_workspace_bytes(const bs_column *proj) {
+    if (!proj) return 0;
+    return bs::scan_lookup_workspace_bytes(proj->c);
+}
+
+int bs_scan_lookup(const bs_pred *preds, int32_t npreds, const bs_column *proj, uint32_t *d_bits, int32_t *d_out,
+                   uint64_t out_cap, uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes, void *stream) {
+    if (!preds || npreds < 1 || npreds > BS_MAX_CONJ) return BS_ERR_INVALID_ARG;
+    if (!proj) proj = preds[0].col;
+    if (!proj) return BS_ERR_INVALID_ARG;
+    if (proj->c.raw || !on_device(proj)) return BS_ERR_UNSUPPORTED;
+    const Column *cols[BS_MAX_CONJ];
+    bs::KPred kp[BS_MAX_CONJ];
+    for (int i = 0; i < npreds; i++) {
+        const bs_column *col = preds[i].col;
+        if (!col || !valid_op(preds[i].op)) return BS_ERR_INVALID_ARG;
+        if (col->c.n != proj->c.n || col->c.device != proj->c.device) return BS_ERR_INVALID_ARG;
+        if (col->c.raw || !on_device(col)) return BS_ERR_UNSUPPORTED;
+        const int rc = bs::rewrite_literal(col->c, preds[i].op, preds[i].lit, preds[i].lit2, kp[i]);
+        if (rc) return rc;
+        cols[i] = &col->c;
+    }
+    if (out_cap && !d_out) return BS_ERR_INVALID_ARG;
+    DeviceGuard g(proj->c.device);
+    if (!g.ok) return BS_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t need = bs::scan_lookup_workspace_bytes(proj->c);
+    void *ws = d_workspace;
+    if (ws && workspace_bytes < need) return BS_ERR_CAPACITY;
+    bool own = false;
+    if (!ws) {
+        if (cudaMallocAsync(&ws, need, s) != cudaSuccess) {
+            cudaGetLastError();
+            return BS_ERR_OOM;
+        }
+        own = true;
+    }
+    const int rc = bs::launch_scan_lookup(cols, kp, npreds, proj->c, d_bits, d_out, out_cap, d_count, ws, s);
+    if (own) cudaFreeAsync(ws, s);
+    return rc;
+}
+
 int bs_lookup_shape(const bs_column *col, int32_t *parts, int32_t *grid, int32_t *resident_ctas) {
     if (!col) return BS_ERR_INVALID_ARG;
     if (!on_device(col)) return BS_ERR_UNSUPPORTED;

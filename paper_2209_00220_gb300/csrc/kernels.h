@@ -26,6 +26,14 @@ int launch_lookup(const Column &c, const uint32_t *d_bits, int32_t *d_vals, uint
 int lookup_shape(const Column &c, uint32_t *parts, uint32_t *grid, uint32_t *resident);
 int launch_lookup_rowids(const Column &c, const uint32_t *d_rowids, uint64_t m, int32_t *d_out, cudaStream_t s);
 
+// Fused conjunction + lookup (fused.cu): cols[p] with predicate kp[p], p <
+// npred (1..4, equal lengths), then the values of `proj` at the selected rows
+// in ascending row order; d_bits (optional) also receives the result bit
+// vector. d_ws: scan_lookup_workspace_bytes(proj) bytes, cleared by the call.
+uint64_t scan_lookup_workspace_bytes(const Column &proj);
+int launch_scan_lookup(const Column *const *cols, const KPred *kp, int npred, const Column &proj, uint32_t *d_bits,
+                       int32_t *d_out, uint64_t out_cap, uint64_t *d_count, void *d_ws, cudaStream_t s);
+
 int read_and_clear_status(uint32_t *status);
 // Device address of the status word on the current device (nullptr on error).
 uint32_t *status_word();

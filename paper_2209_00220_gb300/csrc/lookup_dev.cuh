@@ -695,6 +695,29 @@ __device__ __forceinline__ void gather_chunk(const LookK &a, uint32_t c, uint64_
     }
 }
 
+// One tile with `tc` selected rows (sel: the lane's word) whose first output
+// slot is `base`, by the same per-tile paths as a dense chunk of
+// gather_chunk: staged BS_1 / BS_2 for dense PP-VBS tiles of codes up to two
+// (or, numerical, four) bytes, the listed-rows path otherwise. The tile's
+// off_2 entries are loaded here (gather_chunk can hold a chunk's in registers).
+template <int LAYOUT, int KMAX>
+__device__ __forceinline__ void gather_one_tile(const LookK &a, uint64_t t, uint32_t sel, uint32_t tc, uint64_t base,
+                                                WarpSmemT<KMAX> &sm, const int32_t *val1, uint32_t lane) {
+    constexpr bool kK2 = LAYOUT == BS_PPVBS && KMAX == 2;
+    constexpr bool kK4 = LAYOUT == BS_PPVBS && KMAX == 4;
+    if (kK2 && tc >= kStageMin) {
+        const uint64_t e = t * kGroupsPerTile;
+        const bool has2 = a.K >= 2;
+        const uint32_t goff = has2 ? __ldg(a.off[2] + e + (lane >> 3)) : 0u;
+        const uint32_t lo = has2 ? __ldg(a.off[2] + e) : 0u, hi = has2 ? __ldg(a.off[2] + e + kGroupsPerTile) : 0u;
+        gather_dense_k2(a, t, sel, base, goff, lo, hi, reinterpret_cast<WarpSmemT<2> &>(sm), val1, lane);
+    } else if (kK4 && tc >= kStageMin && !a.categorical) {
+        gather_dense_k4(a, t, sel, base, reinterpret_cast<WarpSmemT<4> &>(sm), val1, lane);
+    } else {
+        gather_tile<LAYOUT, false, KMAX>(a, t, sel, base, sm, val1, lane);
+    }
+}
+
 // LookK view of a column (the per-call fields are filled by the caller).
 inline LookK make_look_args(const Column &c) {
     LookK a{};

@@ -272,8 +272,9 @@ def test_constant_column_and_capacity(B):
 @pytest.mark.slow
 def test_full_size_sweep_column(B):
     """2^30 rows, d = 12, Zipf 1.0, PP-VBS, as bench.py times it: the whole bit
-    vector and every looked-up value against the oracle, which decodes every
-    row from its own layout of the column (about a minute of host time)."""
+    vector and every looked-up value of bs_scan + bs_lookup and of the fused
+    bs_scan_lookup against the oracle, which decodes every row from its own
+    layout of the column (about a minute of host time)."""
     import torch
     n = 1 << 30
     v = synth.config_sweep_column(n, 12, 1.0, 0)
@@ -284,7 +285,14 @@ def test_full_size_sweep_column(B):
     torch.cuda.synchronize()
     got_bits = _bits(bits, n)
     got_vals = vals[: int(cnt.item())].cpu().numpy()
-    del vals, bits, col
+    # the fused scan + lookup on the same column, bit vector included
+    fbits = torch.empty_like(bits)
+    fvals, fcnt = B.bs_scan_lookup([(col, "lt", lit)], out=vals, bits=fbits)
+    torch.cuda.synchronize()
+    assert int(fcnt.item()) == got_vals.size
+    assert torch.equal(fbits, bits)
+    fused_vals = fvals[: int(fcnt.item())].cpu().numpy()
+    del vals, bits, fbits, fvals, col
     ocol = orc.OracleColumn(v, "ppvbs")
     dec = ocol.decode_values()
     del ocol
@@ -293,4 +301,5 @@ def test_full_size_sweep_column(B):
     want_vals = orc.lookup(dec, want)
     assert got_vals.size == want_vals.size
     assert np.array_equal(got_vals, want_vals)
+    assert np.array_equal(fused_vals, want_vals)
     _check_clean(B)
