@@ -45,6 +45,7 @@ sys.path.insert(0, ROOT)
 OUT_DIR = os.environ.get("BENCH_OUT_DIR") or __import__("tempfile").gettempdir()
 
 METRIC = "scan Grows/s & % of HBM roofline; lookup Gvals/s; batched p50/p99 latency"
+WORKLOAD = "sweep column d=12 Zipf s=1.0 PP-VBS, v < c at 10% + lookup"
 
 
 def _peaks():
@@ -190,18 +191,47 @@ def make_column(n, seed):
     return values, lit
 
 
-def oracle_sample(values, lit, rows):
+def oracle_sample(values, lit, rows, threads=1):
     """Time the oracle pipeline on the first `rows` rows: build the plain PP-VBS
-    layout (not timed), then decode every row, scan, look up."""
+    layout (not timed), then decode every row, scan, look up. With threads > 1
+    the rows are split into that many ranges (multiples of 32 rows), each run
+    by the oracle's own sequential code on a thread of its own (the oracle's C
+    calls release the interpreter lock): the range decoder starts its cursors
+    where a full pass has them, and the per-range values are concatenated.
+    Returns (Grows/s, values found, seconds, threads used)."""
+    from concurrent.futures import ThreadPoolExecutor
     from oracle import oracle as orc
     v = values[:rows]
     ocol = orc.OracleColumn(v, "ppvbs")
-    t0 = time.perf_counter()
-    dec = ocol.decode_values()
-    bits = orc.scan_values(dec, "lt", lit)
-    out = orc.lookup(dec, bits)
-    dt = time.perf_counter() - t0
-    return rows / dt / 1e9, int(out.size), dt
+    if threads <= 1:
+        t0 = time.perf_counter()
+        dec = ocol.decode_values()
+        bits = orc.scan_values(dec, "lt", lit)
+        out = orc.lookup(dec, bits)
+        dt = time.perf_counter() - t0
+        return rows / dt / 1e9, int(out.size), dt, 1
+    per = ((rows + threads - 1) // threads + 31) // 32 * 32
+    ranges = [(a, min(a + per, rows)) for a in range(0, rows, per)]
+    ocol.decode_values_range(0, 0)  # prepares the flat layout arrays (not timed)
+
+    def part(r):
+        dec = ocol.decode_values_range(r[0], r[1])
+        bits = orc.scan_values(dec, "lt", lit)
+        return orc.lookup(dec, bits)
+
+    with ThreadPoolExecutor(len(ranges)) as ex:
+        t0 = time.perf_counter()
+        outs = list(ex.map(part, ranges))
+        out = np.concatenate(outs)
+        dt = time.perf_counter() - t0
+    return rows / dt / 1e9, int(out.size), dt, len(ranges)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 # ------------------------------------------------------------ batched form
@@ -528,11 +558,13 @@ def run_reference(args):
     n = 1 << 30
     rows = args.ref_rows
     values, lit = make_column(rows, 0)
+    threads = host_cores()
     for _ in range(args.warmup):
-        oracle_sample(values, lit, rows)
+        oracle_sample(values, lit, rows, threads)
     times = []
+    used = 1
     for _ in range(args.steps):
-        g, m, dt = oracle_sample(values, lit, rows)
+        g, m, dt, used = oracle_sample(values, lit, rows, threads)
         times.append(dt)
     t = float(np.sum(times))
     value = rows * args.steps / t / 1e9
@@ -540,10 +572,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": "sweep column d=12 Zipf s=1.0 PP-VBS, v < c at 10% + lookup",
-                       "rows": n, "sample_rows": rows},
-            "cpu_baseline": {"value": round(value, 6), "unit": "Grows/s", "cores": 1, "kind": "oracle",
-                             "sample": "first %d rows of the same column, every step" % rows},
+            "config": {"workload": WORKLOAD, "rows": n, "sample_rows": rows},
+            "cpu_baseline": {"value": round(value, 6), "unit": "Grows/s", "cores": used, "kind": "oracle",
+                             "sample": "first %d rows of the same column, every step, %d threads over row ranges"
+                                       % (rows, used)},
             "e2e": {"value": round(value, 6), "unit": "Grows/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -553,6 +585,18 @@ def run_reference(args):
 def _scaled(full_traffic, n):
     """Traffic quoted for the 2^30-row bench column, for the rows actually run."""
     return None if full_traffic is None else int(round(full_traffic * n / float(1 << 30)))
+
+
+def _timed(stream, fn, steps):
+    """Per-step CUDA-event times (ms) of `steps` calls of fn on `stream`."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    for i in range(steps):
+        ev[i].record(stream)
+        fn()
+    ev[steps].record(stream)
+    torch.cuda.synchronize()
+    return [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
 
 
 def run_ours(args):
@@ -577,13 +621,14 @@ def run_ours(args):
     m_est = int(np.count_nonzero(values[: 1 << 22] < lit) / min(n, 1 << 22) * n * 1.05) + 1024
     out = torch.empty(min(n, m_est), dtype=torch.int32, device="cuda")
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
-    wsb = B.bs_lookup_workspace_bytes(col)
-    work = torch.empty(wsb // 4 + 1, dtype=torch.int32, device="cuda")
+    fws = torch.empty(B.bs_scan_lookup_workspace_bytes(col) // 4 + 1, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
+    pred = [(col, "lt", lit)]
 
+    # the step: the whole query in the fused kernel -- the predicate's result
+    # bit vector, the values of the selected rows and their count
     def step():
-        B.bs_scan(col, "lt", lit, 0, out=bits, stream=stream)
-        B.bs_lookup(col, bits, out=out, count=count, workspace=work, stream=stream)
+        B.bs_scan_lookup(pred, out=out, count=count, bits=bits, workspace=fws, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -595,8 +640,7 @@ def run_ours(args):
             step()
         torch.cuda.synchronize()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     clocks = Clocks(local)
     if dist:
         dist.barrier()
@@ -606,27 +650,41 @@ def run_ours(args):
         end = torch.cuda.Event(enable_timing=True)
         start.record(stream)
         for i in range(args.steps):
-            ev[i][0].record(stream)
-            B.bs_scan(col, "lt", lit, 0, out=bits, stream=stream)
-            ev[i][1].record(stream)
-            B.bs_lookup(col, bits, out=out, count=count, workspace=work, stream=stream)
-            ev[i][2].record(stream)
+            ev[i].record(stream)
+            step()
+        ev[args.steps].record(stream)
         end.record(stream)
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
     total_ms = start.elapsed_time(end)
-    scan_ms = [a.elapsed_time(b) for a, b, _ in ev]
-    look_ms = [b.elapsed_time(c) for _, b, c in ev]
+    fused_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     t = torch.tensor([total_ms], device="cuda")
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
+    h_bits = bits.cpu()
+
+    # the same query as the paper's operators: scan kernel -> bit vector ->
+    # lookup kernels (count, offsets, gather); its results must be identical
+    ubits = torch.empty_like(bits)
+    uout = torch.empty_like(out)
+    ucount = torch.zeros_like(count)
+    work = torch.empty(B.bs_lookup_workspace_bytes(col) // 4 + 1, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        B.bs_scan(col, "lt", lit, 0, out=ubits, stream=stream)
+        B.bs_lookup(col, ubits, out=uout, count=ucount, workspace=work, stream=stream)
+    scan_ms = _timed(stream, lambda: B.bs_scan(col, "lt", lit, 0, out=ubits, stream=stream), args.steps)
+    look_ms = _timed(stream, lambda: B.bs_lookup(col, ubits, out=uout, count=ucount, workspace=work,
+                                                   stream=stream), args.steps)
+    same_as_unfused = int(ucount.item()) == m and bool(torch.equal(ubits, bits)) and \
+        bool(torch.equal(uout[:m], out[:m]))
+    del ubits, uout, work
 
     # end to end through the public API: every step's result (the count and the
     # whole value buffer, copied without a host round trip for the count) lands
     # in pinned host memory; two result buffers alternate so that one step's
-    # copy overlaps the next step's kernels
+    # copy overlaps the next step's kernel
     cap = out.numel()
     outs = [out, torch.empty_like(out)]
     cnts = [count, torch.zeros_like(count)]
@@ -641,8 +699,7 @@ def run_ours(args):
         k = i % 2
         if freed[k] is not None:
             stream.wait_event(freed[k])  # buffer k's previous copy is done
-        B.bs_scan(col, "lt", lit, 0, out=bits, stream=stream)
-        B.bs_lookup(col, bits, out=outs[k], count=cnts[k], workspace=work, stream=stream)
+        B.bs_scan_lookup(pred, out=outs[k], count=cnts[k], bits=bits, workspace=fws, stream=stream)
         ready = torch.cuda.Event()
         ready.record(stream)
         copier.wait_event(ready)
@@ -654,69 +711,89 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - e0) / e2e_steps
     h_cnt = h_cnts[(e2e_steps - 1) % 2]
-    h_bits = bits.cpu()
     e2e_ok = int(h_cnt.item()) == m and bool(torch.equal(h_outs[0][:m], h_outs[1][:m]))
 
     # correctness of what was timed: the count and a sample of the bit vector
     from oracle import oracle as orc
     samp = slice(0, 1 << 20)
     want = orc.scan_values(values[samp], "lt", lit)
-    ok = bool(np.array_equal(bits[: want.size].cpu().numpy().view(np.uint32), want)) and \
-        int(h_cnt.item()) == int(np.count_nonzero(values < lit)) and e2e_ok
+    ok = bool(np.array_equal(h_bits[: want.size].numpy().view(np.uint32), want)) and \
+        int(h_cnt.item()) == int(np.count_nonzero(values < lit)) and e2e_ok and same_as_unfused
 
     hbm, peak_kind = _peaks()
+    hb = h_bits.numpy().view(np.uint32)
+    fused_bytes = B.bs_scan_lookup_bytes(col, "lt", lit, 0, hb, write_bits=True)["bytes"]
     scan_bytes = B.bs_scan_bytes(col, "lt", lit)["bytes"]
-    look_bytes = B.bs_lookup_bytes(col, h_bits.numpy().view(np.uint32))["bytes"]
-    scan_avg_s = float(np.mean(scan_ms)) / 1e3
-    look_avg_s = float(np.mean(look_ms)) / 1e3
-    achieved = scan_bytes / scan_avg_s / 1e9
-    look_achieved = look_bytes / look_avg_s / 1e9
+    look_bytes = B.bs_lookup_bytes(col, hb)["bytes"]
+    fused_s = float(np.mean(fused_ms)) / 1e3
+    scan_s = float(np.mean(scan_ms)) / 1e3
+    look_s = float(np.mean(look_ms)) / 1e3
     value = n * ws * args.steps / (total_ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "Grows/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "sweep column d=12 Zipf s=1.0 PP-VBS, v < c at 10% + lookup",
+        "config": {"workload": WORKLOAD,
                    "rows_per_gpu": n, "selected": m, "selectivity": round(m / n, 5), "K": info["max_code_bytes"],
+                   "step": "bs_scan_lookup: result bit vector + values + count in one kernel",
                    "l2": "inputs larger than L2 (BS_1 = %d MB), no flush" % (n >> 20),
                    "parallelism": "row shards, replicas" if ws > 1 else "single GPU",
                    "host_numa_node": numa},
-        "scan_grows_s": round(n / scan_avg_s / 1e9, 3),
-        "scan_ms": round(float(np.median(scan_ms)), 4),
-        "lookup_gvals_s": round(m / (float(np.mean(look_ms)) / 1e3) / 1e9, 3),
-        "lookup_ms": round(float(np.median(look_ms)), 4),
-        # the lookup (count + offsets + gather kernels) takes most of the step
-        "roofline": {"bound": "hbm", "achieved": round(look_achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(look_achieved / hbm, 4),
-                     "traffic": _scaled(profile_traffic("lookup_ppvbs_k2_sweep"), n),
-                     "kernel": "bs_lookup: lookup_count + lookup_scan + lookup_gather<PP-VBS, K<=2>",
-                     "peak_kind": peak_kind, "algorithmic_bytes": int(look_bytes)},
-        "roofline_scan": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                          "frac": round(achieved / hbm, 4),
-                          "traffic": _scaled(profile_traffic("scan_dense_ppvbs_sweep"), n),
-                          "kernel": "scan_dense_kernel<PP-VBS>", "peak_kind": peak_kind,
-                          "algorithmic_bytes": int(scan_bytes)},
+        "scan_grows_s": round(n / fused_s / 1e9, 3),
+        "lookup_gvals_s": round(m / fused_s / 1e9, 3),
+        # the fused kernel is the whole step
+        "roofline": {"bound": "hbm", "achieved": round(fused_bytes / fused_s / 1e9, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(fused_bytes / fused_s / 1e9 / hbm, 4),
+                     "traffic": _scaled(profile_traffic("fused_ppvbs_k2_sweep"), n),
+                     "kernel": "fused_kernel<K<=2, v < c> (bs_scan_lookup)", "peak_kind": peak_kind,
+                     "algorithmic_bytes": int(fused_bytes)},
+        "unfused": {
+            "step_ms": round(float(np.median(scan_ms)) + float(np.median(look_ms)), 4),
+            "grows_s": round(n / (scan_s + look_s) / 1e9, 3),
+            "scan_ms": round(float(np.median(scan_ms)), 4), "lookup_ms": round(float(np.median(look_ms)), 4),
+            "lookup_gvals_s": round(m / look_s / 1e9, 3), "identical_to_fused": same_as_unfused,
+            "roofline_scan": {"bound": "hbm", "achieved": round(scan_bytes / scan_s / 1e9, 1), "peak": hbm,
+                              "unit": "GB/s", "frac": round(scan_bytes / scan_s / 1e9 / hbm, 4),
+                              "traffic": _scaled(profile_traffic("scan_dense_ppvbs_sweep"), n),
+                              "kernel": "scan_dense_kernel<PP-VBS>", "algorithmic_bytes": int(scan_bytes)},
+            "roofline_lookup": {"bound": "hbm", "achieved": round(look_bytes / look_s / 1e9, 1), "peak": hbm,
+                                "unit": "GB/s", "frac": round(look_bytes / look_s / 1e9 / hbm, 4),
+                                "traffic": _scaled(profile_traffic("lookup_ppvbs_k2_sweep"), n),
+                                "kernel": "bs_lookup: lookup_count + lookup_scan + lookup_gather<PP-VBS, K<=2>",
+                                "algorithmic_bytes": int(look_bytes)}},
         "e2e": {"value": round(n / e2e_s / 1e9, 4), "unit": "Grows/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 4 * cap + 8, "steps": e2e_steps,
                 "note": "count + value buffer to pinned host memory each step; copies overlap the next step"},
-        "gpu_launches": args.steps * 4,
+        "gpu_launches": args.steps,
         "clocks": clocks.summary(),
         "encode_s": round(encode_s, 2),
         "parity_sample_ok": ok,
     }
+    del outs, h_outs, out
+    torch.cuda.empty_cache()
+    if not args.no_small:
+        line["small"] = run_small_block(B)
     if not args.no_batched:
-        del out, outs, h_outs
         torch.cuda.empty_cache()
         line["batched"] = run_batched(B)
+    if not args.no_wide:
+        torch.cuda.empty_cache()
+        line["wide_table"] = run_wide_table(B)
     if not args.no_serving:
         torch.cuda.empty_cache()
         line["serving"] = run_serving(B, scale=args.serve_scale)
     if rank == 0 and ws == 1 and not args.no_cpu:
+        cores = host_cores()
         rows = min(n, args.cpu_rows)
-        g, _, dt = oracle_sample(values, lit, rows)
-        line["cpu_baseline"] = {"value": round(g, 6), "unit": "Grows/s", "cores": 1, "kind": "oracle",
-                                "sample": "first %d rows of the bench column, decode + scan + lookup, %.1f s"
-                                          % (rows, dt)}
+        g_all, _, dt_all, used = oracle_sample(values, lit, rows, cores)
+        rows1 = min(n, args.cpu_rows_single)
+        g_one, _, dt_one, _ = oracle_sample(values, lit, rows1, 1)
+        line["cpu_baseline"] = {"value": round(g_all, 6), "unit": "Grows/s", "cores": used, "kind": "oracle",
+                                "sample": "first %d rows of the bench column, decode + scan + lookup on %d threads "
+                                          "over row ranges, %.1f s" % (rows, used, dt_all),
+                                "host_cores": cores,
+                                "single_thread": {"value": round(g_one, 6), "unit": "Grows/s", "cores": 1,
+                                                  "sample": "first %d rows, %.1f s" % (rows1, dt_one)}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -725,59 +802,143 @@ def run_ours(args):
 
 
 # ------------------------------------------- the small L2-resident column
-def run_small(args):
+def run_small_block(B, warmup=3, steps=20):
     """The 2^20-row single-column case (Zipf 1.0 over 65,536 distinct signed
     int32, v < c at about 10 % + lookup of every match) on PP-VBS and on
     ByteSlice with its declared 16-bit domain. Its 1 MB of BS_1 lives in L2,
     so each call is timed twice: warm (repeated back to back) and with L2
     flushed before every repetition (a 256 MB buffer written in between); no
-    HBM roofline is claimed here. One JSON line per layout."""
+    HBM roofline is claimed here. Scan, lookup and the fused scan + lookup are
+    timed alone; the values are checked against the plain filter."""
     import torch
-    from paper_2209_00220_gb300 import bytestore as B, synth
+    from paper_2209_00220_gb300 import synth
     n = 1 << 20
     values, domain = synth.config_single_column(seed=0, n=n)
     lit, _ = synth.pick_literals(values, "lt", 0.10, 0)
+    want = values[values < lit]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {"workload": "single column, 2^20 rows, Zipf 1.0 over 65,536 values, v < c + lookup", "rows": n,
+           "selected": int(want.size), "selectivity": round(want.size / n, 5)}
     for lay, opts in (("ppvbs", {}), ("byteslice", {"domain_values": domain})):
         col = B.bs_encode_column(values, lay, **opts)
         bits = torch.empty(col.n_words, dtype=torch.int32, device="cuda")
         out = torch.empty(n, dtype=torch.int32, device="cuda")
+        fout = torch.empty(n, dtype=torch.int32, device="cuda")
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        fcnt = torch.zeros(1, dtype=torch.int64, device="cuda")
         ws = torch.empty(B.bs_lookup_workspace_bytes(col) // 4 + 1, dtype=torch.int32, device="cuda")
-
-        def scan():
-            B.bs_scan(col, "lt", lit, out=bits, stream=stream)
-
-        def look():
-            B.bs_lookup(col, bits, out=out, count=cnt, workspace=ws, stream=stream)
-
-        line = {"workload": "single column, 2^20 rows, Zipf 1.0 over 65,536 values, v < c + lookup",
-                "layout": lay, "rows": n}
+        fws = torch.empty(B.bs_scan_lookup_workspace_bytes(col) // 4 + 1, dtype=torch.int32, device="cuda")
+        fns = (("scan", lambda: B.bs_scan(col, "lt", lit, out=bits, stream=stream)),
+               ("lookup", lambda: B.bs_lookup(col, bits, out=out, count=cnt, workspace=ws, stream=stream)),
+               ("fused", lambda: B.bs_scan_lookup([(col, "lt", lit)], out=fout, count=fcnt, workspace=fws,
+                                                  stream=stream)))
+        r = {}
         for mode in ("warm", "l2_flushed"):
-            for name, fn in (("scan", scan), ("lookup", look)):
+            for name, fn in fns:
                 ts = []
-                for i in range(args.warmup + args.steps):
+                for i in range(warmup + steps):
                     if mode == "l2_flushed":
                         flush.fill_(i & 255)
                     e0.record(stream)
                     fn()
                     e1.record(stream)
                     e1.synchronize()
-                    if i >= args.warmup:
+                    if i >= warmup:
                         ts.append(e0.elapsed_time(e1))
-                line["%s_%s_us" % (name, mode)] = round(1e3 * float(np.median(ts)), 2)
-        m = int(cnt.item())
-        want = values[values < lit]
-        line["selected"] = m
-        line["selectivity"] = round(m / n, 5)
-        line["parity"] = bool(m == want.size and np.array_equal(out[:m].cpu().numpy(), want))
-        line["scan_grows_s_warm"] = round(n / (line["scan_warm_us"] * 1e3), 2)
-        line["lookup_gvals_s_warm"] = round(m / (line["lookup_warm_us"] * 1e3), 2)
-        print(json.dumps(line), flush=True)
+                r["%s_%s_us" % (name, mode)] = round(1e3 * float(np.median(ts)), 2)
+        m, fm = int(cnt.item()), int(fcnt.item())
+        r["parity"] = bool(m == want.size and fm == want.size and np.array_equal(out[:m].cpu().numpy(), want)
+                           and np.array_equal(fout[:fm].cpu().numpy(), want))
+        r["scan_grows_s_warm"] = round(n / (r["scan_warm_us"] * 1e3), 2)
+        r["lookup_gvals_s_warm"] = round(m / (r["lookup_warm_us"] * 1e3), 2)
+        r["fused_grows_s_warm"] = round(n / (r["fused_warm_us"] * 1e3), 2)
+        res[lay] = r
         del col
+    return res
+
+
+def run_small(args):
+    """--small: the single-column block alone, one JSON line."""
+    from paper_2209_00220_gb300 import bytestore as B
+    print(json.dumps(run_small_block(B, warmup=args.warmup, steps=args.steps)), flush=True)
     return 0
+
+
+# ---------------------------------------------- the synthetic wide table
+def run_wide_table(B, n=1 << 26, queries=24, seed=6, advise_rows=1 << 22):
+    """20 int32 columns (categorical, date-like, a monotone id, heavy-tailed
+    amounts, mixed; synth.WIDE_TABLE), each in the layout the advisor's
+    deterministic mode picks from its first 2^22 rows; seeded conjunctions of
+    1-4 predicates followed by lookups of 2-4 projected columns. Each query runs
+    (a) as bs_scan_conj + one bs_lookup per projection and (b) as one fused
+    bs_scan_lookup for the first projection (which also writes the bit vector)
+    + bs_lookup for the others; both are timed per query (CUDA events) and
+    their values compared."""
+    import torch
+    from paper_2209_00220_gb300 import synth
+    names = [w[0] for w in synth.WIDE_TABLE]
+    t0 = time.time()
+    vals, cols, layouts = [], [], []
+    for nm in names:
+        v = synth.wide_table_column(nm, n, 1)
+        lay = B.bs_advise_layout(v[:advise_rows], B.ADVISE_BYTES_MODEL, host_only=True)["layout"]
+        cols.append(B.bs_encode_column(v, lay))
+        vals.append(v[:1 << 20].copy())  # a sample for literals
+        layouts.append(lay)
+        del v
+    setup_s = time.time() - t0
+    r = synth.u64(seed, 77, 16 * queries)
+    stream = torch.cuda.current_stream()
+    bits = torch.empty((n + 31) // 32, dtype=torch.int32, device="cuda")
+    bits2 = torch.empty_like(bits)
+    outs = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(4)]
+    outs2 = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(4)]
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    cnt2 = torch.zeros(4, dtype=torch.int64, device="cuda")
+    lws = torch.empty(max(B.bs_lookup_workspace_bytes(c) for c in cols) // 4 + 1, dtype=torch.int32, device="cuda")
+    fws = torch.empty(max(B.bs_scan_lookup_workspace_bytes(c) for c in cols) // 4 + 1, dtype=torch.int32,
+                      device="cuda")
+    t_plain, t_fused, same, rows_sel = [], [], True, 0
+    for i in range(queries):
+        order = synth.permutation(len(names), seed * 1000 + i)
+        npred = 1 + int(r[i] % np.uint64(4))
+        nproj = 2 + int(r[queries + i] % np.uint64(3))
+        preds = []
+        for j in range(npred):
+            ci = int(order[j])
+            op = ("lt", "eq", "between")[int(r[(2 + j) * queries + i] % np.uint64(3))]
+            tgt = 10 ** (-2 + 1.8 * float(r[(6 + j) * queries + i] >> np.uint64(11)) / float(1 << 53))
+            a, b = synth.pick_literals(vals[ci], op, tgt, seed + i * 4 + j)
+            preds.append((cols[ci], op, a, b))
+        proj = [cols[int(x)] for x in order[len(names) - nproj:]]
+
+        def plain():
+            B.bs_scan_conj(preds, out=bits, stream=stream)
+            for k, pc in enumerate(proj):
+                B.bs_lookup(pc, bits, out=outs[k], count=cnt[k:k + 1], workspace=lws, stream=stream)
+
+        def fused():
+            B.bs_scan_lookup(preds, proj=proj[0], out=outs2[0], count=cnt2[0:1], bits=bits2, workspace=fws,
+                             stream=stream)
+            for k, pc in enumerate(proj[1:], 1):
+                B.bs_lookup(pc, bits2, out=outs2[k], count=cnt2[k:k + 1], workspace=lws, stream=stream)
+
+        plain()
+        fused()
+        t_plain.append(float(np.median(_timed(stream, plain, 3))))
+        t_fused.append(float(np.median(_timed(stream, fused, 3))))
+        c = cnt.cpu().numpy()
+        rows_sel += int(c[0])
+        same = same and bool(torch.equal(cnt[:nproj], cnt2[:nproj])) and bool(torch.equal(bits, bits2)) and all(
+            torch.equal(outs[k][:int(c[k])], outs2[k][:int(c[k])]) for k in range(nproj))
+    tp, tf = float(np.sum(t_plain)), float(np.sum(t_fused))
+    return {"rows": n, "columns": len(names), "layouts": {l: layouts.count(l) for l in set(layouts)},
+            "queries": queries, "setup_s": round(setup_s, 1), "selected_rows": rows_sel,
+            "plain_ms_total": round(tp, 3), "fused_ms_total": round(tf, 3), "speedup": round(tp / tf, 3),
+            "plain_ms_per_query": round(tp / queries, 4), "fused_ms_per_query": round(tf / queries, 4),
+            "identical": same}
 
 
 # --------------------------------------------------- the full layout sweep
@@ -855,7 +1016,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rows", type=int, default=1 << 30)
     ap.add_argument("--ref-rows", type=int, default=1 << 24, help="oracle rows per step of --impl reference")
-    ap.add_argument("--cpu-rows", type=int, default=1 << 28, help="oracle rows timed for cpu_baseline")
+    ap.add_argument("--cpu-rows", type=int, default=1 << 28, help="oracle rows timed on all host cores")
+    ap.add_argument("--cpu-rows-single", type=int, default=1 << 26, help="oracle rows timed on one core")
+    ap.add_argument("--no-small", action="store_true", help="skip the 2^20-row single-column block")
+    ap.add_argument("--no-wide", action="store_true", help="skip the wide-table block")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-request batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")

@@ -237,7 +237,7 @@ int bs_lookup_codes(const bs_column *col, const uint32_t *d_bits, uint64_t *d_co
 /* ------------------------------------------------- fused scan + lookup */
 
 /* Device workspace bytes bs_scan_lookup needs for a projection column of this
- * length (8 bytes per 2048 rows plus 256). */
+ * length (8 bytes per 1024 rows plus 256). */
 uint64_t bs_scan_lookup_workspace_bytes(const bs_column *proj);
 
 /* Fused scan + lookup (Section 2.2's query shape: a conjunction of predicates
@@ -383,20 +383,41 @@ typedef struct {
                                result; NULL = batch-owned scratch */
 } bs_request;
 
-/* Shape of the batched launch (NULL = defaults).
+/* Shape of the batched launch (NULL = defaults; any shape field set makes the
+ * shape explicit: the unset ones take their defaults, no cache is read).
  *   threads: 128, 256 or 512 threads per CTA; 0 = the tuned (or default 256) shape.
  *   blocks_per_sm: CTAs per SM, 0 = as many as fit (all CTAs are co-resident).
- *   autotune: 1 = time the candidate shapes on this batch and keep the fastest;
- *             the choice is cached per batch signature in tune_cache.
+ *   autotune: 1 = time candidate shapes on this batch and keep the fastest:
+ *             threads x CTAs per SM, then around the best the ring stages,
+ *             the chunks per claim and the early-stop granularity; the choice
+ *             is cached per batch signature in tune_cache.
  *   use_graph: 1 (default) = capture the launch in a CUDA graph, 0 = launch directly.
- *   tune_cache: JSON-lines cache file, NULL = $BS_TUNE_CACHE (or no cache). */
+ *   tune_cache: JSON-lines cache file, NULL = $BS_TUNE_CACHE (or no cache).
+ *   stages: slices of the first predicate in flight per warp (2, 3 or 4; 0 = 3).
+ *   unit_chunks: chunks of 16 tiles (16,384 rows) a warp takes per claim, i.e.
+ *             rows per unit of work (1, 2 or 4; 0 = 1).
+ *   stop_rows: early-stop granularity, the rows whose pending state decides
+ *             whether a deeper level is read: 256 (one PP-VBS mask group, or
+ *             the lanes of a ByteSlice tile that have pending rows) or 1024
+ *             (the whole tile once any row is pending); 0 = 256. */
 typedef struct {
     int32_t threads;
     int32_t blocks_per_sm;
     int32_t autotune;
     int32_t use_graph;
     const char *tune_cache;
+    int32_t stages;
+    int32_t unit_chunks;
+    int32_t stop_rows;
+    int32_t reserved;
 } bs_batch_opts;
+
+/* The shape a batch runs with. */
+typedef struct {
+    int32_t threads, blocks_per_sm, ctas, stages, unit_chunks, stop_rows, graph;
+    int32_t persistent_requests;     /* requests run by the persistent kernel */
+    int32_t single_query_requests;   /* requests run by the single-query kernels (columns of 2^28+ rows) */
+} bs_batch_shape;
 
 typedef struct bs_batch bs_batch; /* opaque: descriptors, scratch, captured graph */
 
@@ -417,6 +438,9 @@ int bs_batch_launch(bs_batch *b, void *stream);
 
 /* The shape the batch runs with: threads per CTA, CTAs, graph captured (0/1). */
 int bs_batch_info(const bs_batch *b, int32_t *threads, int32_t *ctas, int32_t *graph);
+
+/* The full launch shape of a batch (including the tuned parameters). */
+int bs_batch_get_shape(const bs_batch *b, bs_batch_shape *out);
 
 void bs_batch_free(bs_batch *b);
 
@@ -442,7 +466,10 @@ typedef struct {
  *   streams (2); result_bytes: device memory for result buffers, the admission
  *   cap (1 GiB); scratch_bytes: device memory for the bit vectors and chunk
  *   offsets of queries in flight (4 GiB); threads: batch kernel CTA size (256);
- *   device: CUDA device, -1 = current. */
+ *   device: CUDA device, -1 = current; single_query_kernels: 1 = every query
+ *   runs the single-query scan and lookup kernels, never the persistent kernel
+ *   (with max_batch = 1 and slots = 1 this is serial plain execution through
+ *   the same dispatcher and admission). */
 typedef struct {
     int32_t max_batch;
     int32_t slots;
@@ -450,6 +477,8 @@ typedef struct {
     uint64_t scratch_bytes;
     int32_t threads;
     int32_t device;
+    int32_t single_query_kernels;
+    int32_t reserved;
 } bs_server_opts;
 
 typedef struct {
@@ -471,6 +500,8 @@ typedef struct {
     uint64_t result_bytes_in_use, scratch_bytes_in_use;
     uint64_t queued;
     uint64_t failed;          /* completed queries whose status is not BS_OK */
+    uint64_t persistent_queries;    /* queries run by the persistent kernel */
+    uint64_t single_query_queries;  /* queries run by the single-query kernels */
 } bs_server_stats;
 
 typedef struct bs_server bs_server; /* opaque */

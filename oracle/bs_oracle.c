@@ -217,16 +217,38 @@ int orc_vbs_build(const uint64_t *codes, const uint8_t *lens, uint64_t n, int K,
     return 0;
 }
 
-/* Sequential decoder: one cursor per slice, advanced whenever a row's mask bit
- * is set. Returns the zero-padded K-byte codes (as integers) and lengths. */
-int orc_vbs_decode(const uint8_t *bs1, const uint32_t *masks, const uint8_t *deep,
-                   const uint64_t *slice_len, uint64_t n, int K, uint64_t *padded, uint8_t *lens) {
+/* Where the sequential decoder's cursors stand at row `row`: cursor[j-2] =
+ * the number of rows before `row` whose mask-j bit is set (whole words
+ * popcounted, then the partial word), j = 2..K. */
+void orc_vbs_cursors_at(const uint32_t *masks, uint64_t n, int K, uint64_t row, uint64_t *cursor) {
+    uint64_t nw = (n + 31) / 32;
+    for (int j = 2; j <= K; j++) {
+        const uint32_t *M = masks + (uint64_t)(j - 2) * nw;
+        uint64_t c = 0;
+        for (uint64_t w = 0; w < row / 32; w++) c += (uint64_t)__builtin_popcount(M[w]);
+        if (row % 32) c += (uint64_t)__builtin_popcount(M[row / 32] & ((1u << (row % 32)) - 1u));
+        cursor[j - 2] = c;
+    }
+}
+
+/* Sequential decoder over rows [r0, r1): one cursor per slice, starting at
+ * cursor0[j-2] (orc_vbs_cursors_at(r0)) and advanced whenever a row's mask
+ * bit is set. Writes the zero-padded K-byte codes (as integers) and lengths
+ * of rows r0.. at padded[0..], lens[0..]. Disjoint ranges decoded separately
+ * give the same codes as one pass over all rows. */
+int orc_vbs_decode_range(const uint8_t *bs1, const uint32_t *masks, const uint8_t *deep,
+                         const uint64_t *slice_len, uint64_t n, int K, uint64_t r0, uint64_t r1,
+                         const uint64_t *cursor0, uint64_t *padded, uint8_t *lens) {
     uint64_t nw = (n + 31) / 32;
     uint64_t start[8], cursor[8];
     uint64_t acc = 0;
-    if (K < 1 || K > 8) return -1;
-    for (int j = 2; j <= K; j++) { start[j] = acc; cursor[j] = 0; acc += slice_len[j - 2]; }
-    for (uint64_t i = 0; i < n; i++) {
+    if (K < 1 || K > 8 || r1 > n || r0 > r1) return -1;
+    for (int j = 2; j <= K; j++) {
+        start[j] = acc;
+        cursor[j] = cursor0 ? cursor0[j - 2] : 0;
+        acc += slice_len[j - 2];
+    }
+    for (uint64_t i = r0; i < r1; i++) {
         uint64_t code = bs1[i];
         int len = 1;
         for (int j = 2; j <= K; j++) {
@@ -238,10 +260,17 @@ int orc_vbs_decode(const uint8_t *bs1, const uint32_t *masks, const uint8_t *dee
                 len = j;
             }
         }
-        padded[i] = code << (8 * (K - len));
-        lens[i] = (uint8_t)len;
+        padded[i - r0] = code << (8 * (K - len));
+        lens[i - r0] = (uint8_t)len;
     }
     return 0;
+}
+
+/* Sequential decoder over all rows. Returns the zero-padded K-byte codes (as
+ * integers) and lengths. */
+int orc_vbs_decode(const uint8_t *bs1, const uint32_t *masks, const uint8_t *deep,
+                   const uint64_t *slice_len, uint64_t n, int K, uint64_t *padded, uint8_t *lens) {
+    return orc_vbs_decode_range(bs1, masks, deep, slice_len, n, K, 0, n, NULL, padded, lens);
 }
 
 /* ------------------------------------------------------ ByteSlice layout */

@@ -52,6 +52,8 @@ def lib():
                 "orc_vbs_slice_lengths": ([vp, u64, ctypes.c_int, vp], None),
                 "orc_vbs_build": ([vp, vp, u64, ctypes.c_int, vp, vp, vp], ctypes.c_int),
                 "orc_vbs_decode": ([vp, vp, vp, vp, u64, ctypes.c_int, vp, vp], ctypes.c_int),
+                "orc_vbs_cursors_at": ([vp, u64, ctypes.c_int, u64, vp], None),
+                "orc_vbs_decode_range": ([vp, vp, vp, vp, u64, ctypes.c_int, u64, u64, vp, vp, vp], ctypes.c_int),
                 "orc_byteslice_build": ([vp, u64, ctypes.c_int, vp], ctypes.c_int),
                 "orc_byteslice_decode": ([vp, u64, ctypes.c_int, vp], ctypes.c_int),
                 "orc_bitpacked_build": ([vp, u64, ctypes.c_int, vp], ctypes.c_int),
@@ -320,6 +322,35 @@ class OracleColumn:
         if self.identity:
             return (codes.astype(np.int64) + self.domain_min).astype(np.int32)
         return self.A[codes.astype(np.int64)]
+
+    def decode_values_range(self, r0: int, r1: int) -> np.ndarray:
+        """Rows [r0, r1) decoded from the layout to their values: the same
+        sequential decoder, its cursors started where a full pass would have
+        them at r0 (PP-VBS only). Disjoint ranges may run on several threads."""
+        if self.layout != "ppvbs":
+            raise ValueError("ranges are decoded for PP-VBS columns")
+        if not hasattr(self, "_flat"):
+            sl = np.array([s.size for s in self.slices] + [0], np.uint64)
+            deep = np.concatenate(self.slices) if self.slices else np.zeros(1, np.uint8)
+            masks = _c(self.masks, np.uint32).reshape(-1)
+            self._flat = (_c(self.bs1, np.uint8), masks if masks.size else np.zeros(1, np.uint32),
+                          _c(deep if deep.size else np.zeros(1, np.uint8), np.uint8), sl)
+        bs1, masks, deep, sl = self._flat
+        cur = np.zeros(8, np.uint64)
+        lib().orc_vbs_cursors_at(_p(masks), self.n, self.K, r0, _p(cur))
+        m = r1 - r0
+        padded = np.zeros(max(1, m), np.uint64)
+        lens = np.zeros(max(1, m), np.uint8)
+        rc = lib().orc_vbs_decode_range(_p(bs1), _p(masks), _p(deep), _p(sl), self.n, self.K, r0, r1, _p(cur),
+                                        _p(padded), _p(lens))
+        if rc != 0:
+            raise ValueError("orc_vbs_decode_range failed (%d)" % rc)
+        out = np.empty(max(1, m), np.int32)
+        sc = _c(self._sorted_codes, np.uint64)
+        sv = _c(self._sorted_vals, np.int32)
+        if lib().orc_codes_to_values(_p(padded), m, _p(sc), _p(sv), sc.size, _p(out)) != 0:
+            raise ValueError("decoded code missing from the dictionary")
+        return out[:m]
 
     def scan(self, op: str, lit: int, lit2: int = 0) -> np.ndarray:
         return scan_values(self.decode_values(), op, lit, lit2)

@@ -61,7 +61,14 @@ class bs_request(ctypes.Structure):
 
 class bs_batch_opts(ctypes.Structure):
     _fields_ = [("threads", _i32), ("blocks_per_sm", _i32), ("autotune", _i32), ("use_graph", _i32),
-                ("tune_cache", ctypes.c_char_p)]
+                ("tune_cache", ctypes.c_char_p), ("stages", _i32), ("unit_chunks", _i32), ("stop_rows", _i32),
+                ("reserved", _i32)]
+
+
+class bs_batch_shape(ctypes.Structure):
+    _fields_ = [("threads", _i32), ("blocks_per_sm", _i32), ("ctas", _i32), ("stages", _i32),
+                ("unit_chunks", _i32), ("stop_rows", _i32), ("graph", _i32), ("persistent_requests", _i32),
+                ("single_query_requests", _i32)]
 
 
 class bs_query(ctypes.Structure):
@@ -70,7 +77,7 @@ class bs_query(ctypes.Structure):
 
 class bs_server_opts(ctypes.Structure):
     _fields_ = [("max_batch", _i32), ("slots", _i32), ("result_bytes", _u64), ("scratch_bytes", _u64),
-                ("threads", _i32), ("device", _i32)]
+                ("threads", _i32), ("device", _i32), ("single_query_kernels", _i32), ("reserved", _i32)]
 
 
 class bs_query_result(ctypes.Structure):
@@ -81,7 +88,7 @@ class bs_query_result(ctypes.Structure):
 class bs_server_stats(ctypes.Structure):
     _fields_ = [("submitted", _u64), ("completed", _u64), ("rejected", _u64), ("batches", _u64),
                 ("mean_batch", ctypes.c_double), ("result_bytes_in_use", _u64), ("scratch_bytes_in_use", _u64),
-                ("queued", _u64), ("failed", _u64)]
+                ("queued", _u64), ("failed", _u64), ("persistent_queries", _u64), ("single_query_queries", _u64)]
 
 
 class bs_advice(ctypes.Structure):
@@ -122,6 +129,7 @@ _SIGS = {
     "bs_batch_launch": ([_vp, _vp], _i32),
     "bs_batch_info": ([_vp, _vp, _vp, _vp], _i32),
     "bs_batch_free": ([_vp], None),
+    "bs_batch_get_shape": ([_vp, _vp], _i32),
     "bs_estimate_rows": ([_vp, _i32, _i32, _i32, _vp], _i32),
     "bs_server_create": ([_vp, _vp], _i32),
     "bs_server_submit": ([_vp, _vp, _vp], _i32),
@@ -508,6 +516,13 @@ class Batch:
         _check(lib().bs_batch_info(self.handle, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g)), "bs_batch_info")
         return {"threads": t.value, "ctas": c.value, "graph": bool(g.value)}
 
+    def shape(self) -> dict:
+        """The full launch shape: threads, blocks_per_sm, ctas, stages,
+        unit_chunks, stop_rows, graph, persistent_requests, single_query_requests."""
+        s = bs_batch_shape()
+        _check(lib().bs_batch_get_shape(self.handle, ctypes.byref(s)), "bs_batch_get_shape")
+        return {name: getattr(s, name) for name, _ in s._fields_}
+
     def __del__(self):
         h, self.handle = getattr(self, "handle", None), None
         if h and _lib is not None:
@@ -518,7 +533,8 @@ class Batch:
 
 
 def bs_batch_create(requests, threads: int = 0, blocks_per_sm: int = 0, autotune: bool = False,
-                    use_graph: bool = True, tune_cache: str | None = None) -> Batch:
+                    use_graph: bool = True, tune_cache: str | None = None, stages: int = 0, unit_chunks: int = 0,
+                    stop_rows: int = 0) -> Batch:
     """requests: sequence of dicts with keys
          preds: [(Column, op, lit[, lit2]), ...]  (1..4, equal-length columns)
          out:   torch int32 CUDA tensor (capacity = its numel unless out_cap given)
@@ -550,6 +566,7 @@ def bs_batch_create(requests, threads: int = 0, blocks_per_sm: int = 0, autotune
     o.threads, o.blocks_per_sm = int(threads), int(blocks_per_sm)
     o.autotune, o.use_graph = 1 if autotune else 0, 1 if use_graph else 0
     o.tune_cache = tune_cache.encode() if tune_cache else None
+    o.stages, o.unit_chunks, o.stop_rows = int(stages), int(unit_chunks), int(stop_rows)
     h = _vp()
     _check(lib().bs_batch_create(arr, len(requests), ctypes.byref(o), ctypes.byref(h)), "bs_batch_create")
     return Batch(h.value, keep)
@@ -654,10 +671,11 @@ class Server:
 
 
 def bs_server_create(max_batch: int = 0, slots: int = 0, result_bytes: int = 0, scratch_bytes: int = 0,
-                     threads: int = 0, device: int = -1) -> Server:
+                     threads: int = 0, device: int = -1, single_query_kernels: bool = False) -> Server:
     o = bs_server_opts()
     o.max_batch, o.slots, o.result_bytes, o.scratch_bytes = max_batch, slots, result_bytes, scratch_bytes
     o.threads, o.device = threads, device
+    o.single_query_kernels = 1 if single_query_kernels else 0
     h = _vp()
     _check(lib().bs_server_create(ctypes.byref(o), ctypes.byref(h)), "bs_server_create")
     return Server(h.value)

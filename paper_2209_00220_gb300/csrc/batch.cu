@@ -76,6 +76,8 @@ struct BatchK {
     int32_t nreq;
     uint32_t total_units;
     uint32_t total_segs;
+    uint32_t unit_chunks;   // chunks a warp takes per claim (1, 2 or 4; rows per claim = 16384 x this)
+    uint32_t total_claims;  // ceil(total_units / unit_chunks)
     uint32_t *ctr;          // [0] scan units claimed, [1] gather units claimed, [2] barrier arrivals
     uint32_t *status;
 };
@@ -84,7 +86,7 @@ union WarpSmemAny {
     WarpSmemT<2> k2;
     WarpSmemT<4> k4;
     WarpSmemT<8> k8;
-    uint8_t ring[kStages][kTileRows];  // phase 1: the first predicate's slice tiles in flight
+    uint8_t ring[kStagesMax][kTileRows];  // phase 1: the first predicate's slice tiles in flight
 };
 
 // Largest r with prefix[r] <= u (prefix: nreq + 1 non-decreasing entries).
@@ -122,18 +124,22 @@ __device__ void grid_barrier(const BatchK &b, uint32_t round) {
 }
 
 // 512-thread CTAs at two per SM at least: at most 64 registers a thread, so a
-// 256-thread shape keeps 32 warps resident per SM.
+// 256-thread shape keeps 32 warps resident per SM. STAGES: slots of the
+// phase-1 ring (tiles of the first predicate's slice in flight per warp).
+template <int STAGES>
 __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchK b) {
+    static_assert(STAGES >= 2 && STAGES <= kStagesMax, "ring slots");
     extern __shared__ __align__(16) unsigned char batch_smem[];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     WarpSmemAny &sm = reinterpret_cast<WarpSmemAny *>(batch_smem)[warp];
 
-    // ---- phase 1: scan every request's chunks
+    // ---- phase 1: scan every request's chunks, unit_chunks of them per claim
     uint8_t *ring = &sm.ring[0][0];
     const uint32_t rbase = (uint32_t)__cvta_generic_to_shared(ring);
     for (;;) {
-        const uint32_t u = claim(b.ctr + 0, lane);
-        if (u >= b.total_units) break;
+        const uint32_t cl = claim(b.ctr + 0, lane);
+        if (cl >= b.total_claims) break;
+        for (uint32_t u = cl * b.unit_chunks; u < min((cl + 1) * b.unit_chunks, b.total_units); u++) {
         const uint32_t r = find_request(b.unit0, b.nreq, u);
         const BReq &R = b.reqs[r];
         const uint32_t c = u - R.unit0;
@@ -154,8 +160,8 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchK b) {
             cp_async_commit();
         };
         if (staged) {
-            issue(t0, 0);
-            issue(t0 + 1, 1);
+#pragma unroll
+            for (int s = 0; s < STAGES - 1; s++) issue(t0 + (uint32_t)s, s);
         }
         int stage = 0;
         uint32_t cnt = 0;
@@ -163,13 +169,14 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchK b) {
             const uint64_t w = (uint64_t)t * kTileWords + lane;
             uint32_t sd = valid_mask(w * 32u, n);
             if (staged) {
-                issue(t + 2, (stage + 2) % kStages);
-                cp_async_wait<kStages - 1>();
+                // the slot of tile t - 1 (read in the previous step) takes tile t + STAGES - 1
+                issue(t + STAGES - 1, (stage + STAGES - 1) % STAGES);
+                cp_async_wait<STAGES - 1>();
                 const uint4 *sp = reinterpret_cast<const uint4 *>(ring + stage * kTileRows);
                 const uint4 v0 = sp[lane], v1 = sp[32 + lane];
                 const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
                 sd = dense_pred(P0, t, lane, x, sd);
-                stage = (stage + 1) % kStages;
+                stage = stage + 1 == STAGES ? 0 : stage + 1;
             } else {
                 sd = pred_tile(P0, t, lane, sd);
             }
@@ -185,6 +192,7 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchK b) {
         if (lane == 0) {
             R.chunk_cnt[c] = cnt;
             if (cnt) atomicAdd((unsigned long long *)(R.seg_tot + c / kSegChunks), (unsigned long long)cnt);
+        }
         }
     }
     grid_barrier(b, 1);
@@ -225,19 +233,27 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchK b) {
     }
     grid_barrier(b, 2);
 
-    // ---- phase 3: gather every request's chunks
+    // ---- phase 3: gather every request's chunks, unit_chunks of them per claim
     for (;;) {
-        const uint32_t u = claim(b.ctr + 1, lane);
-        if (u >= b.total_units) break;
-        const uint32_t r = find_request(b.unit0, b.nreq, u);
-        const BReq &R = b.reqs[r];
-        const uint32_t c = u - R.unit0;
-        const uint64_t base = __ldcg(R.chunk_off + c);
-        if (base >= R.look.out_cap) continue;
-        if (R.kmax == 2) gather_any<2>(R.look, c, base, sm.k2, R.val1, lane);
-        else if (R.kmax == 4) gather_any<4>(R.look, c, base, sm.k4, R.val1, lane);
-        else gather_any<8>(R.look, c, base, sm.k8, R.val1, lane);
+        const uint32_t cl = claim(b.ctr + 1, lane);
+        if (cl >= b.total_claims) break;
+        for (uint32_t u = cl * b.unit_chunks; u < min((cl + 1) * b.unit_chunks, b.total_units); u++) {
+            const uint32_t r = find_request(b.unit0, b.nreq, u);
+            const BReq &R = b.reqs[r];
+            const uint32_t c = u - R.unit0;
+            const uint64_t base = __ldcg(R.chunk_off + c);
+            if (base >= R.look.out_cap) continue;
+            if (R.kmax == 2) gather_any<2>(R.look, c, base, sm.k2, R.val1, lane);
+            else if (R.kmax == 4) gather_any<4>(R.look, c, base, sm.k4, R.val1, lane);
+            else gather_any<8>(R.look, c, base, sm.k8, R.val1, lane);
+        }
     }
+}
+
+using BatchFn = void (*)(const BatchK);
+
+BatchFn batch_fn(int stages) {
+    return stages == 2 ? batch_kernel<2> : (stages == 4 ? batch_kernel<4> : batch_kernel<3>);
 }
 
 // ------------------------------------------------------------ request plan
@@ -355,7 +371,15 @@ std::string tune_path(const bs_batch_opts &o) {
     return e ? std::string(e) : std::string();
 }
 
-bool tune_lookup(const std::string &path, const std::string &key, int &threads, int &bps) {
+// Launch shape of the persistent kernel: the candidates the tuner searches
+// are threads per CTA {128, 256, 512} x CTAs per SM {1, 2, all that fit},
+// then ring stages {2, 3, 4}, chunks per claim {1, 2, 4} and the early-stop
+// granularity {256-row group, 1024-row tile}.
+struct Shape {
+    int threads = 256, bps = 0, stages = kStages, unit_chunks = 1, stop_all = 0;
+};
+
+bool tune_lookup(const std::string &path, const std::string &key, Shape &sh) {
     if (path.empty()) return false;
     std::lock_guard<std::mutex> g(g_tune_mu);
     FILE *f = std::fopen(path.c_str(), "r");
@@ -364,12 +388,17 @@ bool tune_lookup(const std::string &path, const std::string &key, int &threads, 
     bool found = false;
     while (std::fgets(line, sizeof line, f)) {
         char k[512];
-        int t = 0, b = 0;
-        // {"key": "...", "threads": T, "blocks_per_sm": B, ...}
-        if (std::sscanf(line, " {\"key\": \"%511[^\"]\", \"threads\": %d, \"blocks_per_sm\": %d", k, &t, &b) == 3 &&
-            key == k) {
-            threads = t;
-            bps = b;
+        Shape t;
+        int stop_rows = 256;
+        // {"key": "...", "threads": T, "blocks_per_sm": B, "stages": S, "unit_chunks": U, "stop_rows": R, ...}
+        const int got = std::sscanf(line,
+                                    " {\"key\": \"%511[^\"]\", \"threads\": %d, \"blocks_per_sm\": %d, \"stages\": "
+                                    "%d, \"unit_chunks\": %d, \"stop_rows\": %d",
+                                    k, &t.threads, &t.bps, &t.stages, &t.unit_chunks, &stop_rows);
+        if (got >= 3 && key == k) {
+            if (got < 6) t = Shape{t.threads, t.bps};  // an entry from before the wider search
+            t.stop_all = stop_rows >= 1024 ? 1 : 0;
+            sh = t;
             found = true;  // the last entry for a key wins
         }
     }
@@ -377,13 +406,15 @@ bool tune_lookup(const std::string &path, const std::string &key, int &threads, 
     return found;
 }
 
-void tune_store(const std::string &path, const std::string &key, int threads, int bps, double us) {
+void tune_store(const std::string &path, const std::string &key, const Shape &sh, double us) {
     if (path.empty()) return;
     std::lock_guard<std::mutex> g(g_tune_mu);
     FILE *f = std::fopen(path.c_str(), "a");
     if (!f) return;
-    std::fprintf(f, "{\"key\": \"%s\", \"threads\": %d, \"blocks_per_sm\": %d, \"us\": %.2f}\n", key.c_str(), threads,
-                 bps, us);
+    std::fprintf(f,
+                 "{\"key\": \"%s\", \"threads\": %d, \"blocks_per_sm\": %d, \"stages\": %d, \"unit_chunks\": %d, "
+                 "\"stop_rows\": %d, \"us\": %.2f}\n",
+                 key.c_str(), sh.threads, sh.bps, sh.stages, sh.unit_chunks, sh.stop_all ? 1024 : 256, us);
     std::fclose(f);
 }
 
@@ -400,6 +431,8 @@ struct bs_batch {
     size_t zero_bytes = 0;  // counters and segment totals, cleared before every launch
     std::vector<bs::PlainReq> plain;  // requests run by the single-query kernels
     bs::BatchK k{};         // the others (k.nreq may be 0)
+    std::vector<bs::BReq> hreqs;  // host copy of k.reqs (rewritten when the early-stop granularity changes)
+    bs::Shape sh;           // launch shape (ctas follows from it)
     int threads = 256;
     int ctas = 0;
     bool use_graph = true;
@@ -410,11 +443,18 @@ struct bs_batch {
 
 namespace {
 
+int launch_persistent(bs_batch *b, cudaStream_t s);
+
 int launch_direct(bs_batch *b, cudaStream_t s) {
     for (const bs::PlainReq &P : b->plain) {
         const int rc = bs::launch_plain(P, s);
         if (rc) return rc;
     }
+    return launch_persistent(b, s);
+}
+
+// The persistent kernel over the requests it takes (counters cleared first).
+int launch_persistent(bs_batch *b, cudaStream_t s) {
     if (b->k.nreq == 0) return BS_OK;
     if (cudaMemsetAsync(b->k.ctr, 0, b->zero_bytes, s) != cudaSuccess) return BS_ERR_CUDA;
     cudaLaunchConfig_t cfg{};
@@ -427,27 +467,41 @@ int launch_direct(bs_batch *b, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, bs::batch_kernel, b->k);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, bs::batch_fn(b->sh.stages), b->k);
     return e == cudaSuccess ? BS_OK : BS_ERR_CUDA;
 }
 
-int shape(bs_batch *b, int threads, int bps) {
-    if (threads != 128 && threads != 256 && threads != 512) return BS_ERR_INVALID_ARG;
-    const size_t smem = bs::smem_bytes(threads);
-    if (cudaFuncSetAttribute(bs::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
+// Applies a launch shape: occupancy of the chosen kernel variant, the grid,
+// the claim size, and the early-stop granularity written into the request
+// descriptors (uploaded again when it changes).
+int shape(bs_batch *b, const bs::Shape &sh) {
+    if (sh.threads != 128 && sh.threads != 256 && sh.threads != 512) return BS_ERR_INVALID_ARG;
+    if (sh.stages < 2 || sh.stages > bs::kStagesMax) return BS_ERR_INVALID_ARG;
+    if (sh.unit_chunks != 1 && sh.unit_chunks != 2 && sh.unit_chunks != 4) return BS_ERR_INVALID_ARG;
+    const bs::BatchFn fn = bs::batch_fn(sh.stages);
+    const size_t smem = bs::smem_bytes(sh.threads);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return BS_ERR_CUDA;
     }
     int fit = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, bs::batch_kernel, threads, smem) != cudaSuccess ||
-        fit < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, sh.threads, smem) != cudaSuccess || fit < 1) {
         cudaGetLastError();
         return BS_ERR_CUDA;
     }
-    const int per_sm = bps > 0 ? std::min(bps, fit) : fit;
-    b->threads = threads;
+    const int per_sm = sh.bps > 0 ? std::min(sh.bps, fit) : fit;
+    if (b->k.nreq > 0 && (sh.stop_all != b->sh.stop_all || b->hreqs.empty())) {
+        for (bs::BReq &R : b->hreqs)
+            for (int p = 0; p < R.npred; p++) R.pred[p].a.stop_all = (uint32_t)sh.stop_all;
+        if (cudaMemcpy((void *)b->k.reqs, b->hreqs.data(), sizeof(bs::BReq) * b->hreqs.size(),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return BS_ERR_CUDA;
+    }
+    b->sh = sh;
+    b->threads = sh.threads;
     b->ctas = per_sm * bs::sm_count(b->device);
+    b->k.unit_chunks = (uint32_t)sh.unit_chunks;
+    b->k.total_claims = (b->k.total_units + (uint32_t)sh.unit_chunks - 1) / (uint32_t)sh.unit_chunks;
     return BS_OK;
 }
 
@@ -569,8 +623,14 @@ int bs_batch_create(const bs_request *reqs, int32_t nreq, const bs_batch_opts *o
             rc = BS_ERR_CUDA;
     }
     // launch shape: explicit, cached, autotuned or the default
-    int threads = o.threads > 0 ? o.threads : 256, bps = o.blocks_per_sm;
+    Shape sh;
+    if (o.threads > 0) sh.threads = o.threads;
+    sh.bps = o.blocks_per_sm;
+    if (o.stages > 0) sh.stages = o.stages;
+    if (o.unit_chunks > 0) sh.unit_chunks = o.unit_chunks;
+    if (o.stop_rows > 0) sh.stop_all = o.stop_rows >= 1024 ? 1 : 0;
     if (rc == BS_OK) {
+        b->hreqs.assign(hb.begin(), hb.begin() + nb);
         cudaDeviceProp prop{};
         cudaGetDeviceProperties(&prop, device);
         char key[384];
@@ -578,36 +638,66 @@ int bs_batch_create(const bs_request *reqs, int32_t nreq, const bs_batch_opts *o
                       (int)b->plain.size(), total_rows ? 63 - __builtin_clzll(total_rows) : 0, n_layout[BS_PPVBS],
                       n_layout[BS_BYTESLICE], n_layout[BS_BITPACKED]);
         const std::string path = tune_path(o);
-        if (o.threads <= 0 && !o.autotune) tune_lookup(path, key, threads, bps);
+        const bool explicit_shape = o.threads > 0 || o.stages > 0 || o.unit_chunks > 0 || o.stop_rows > 0;
+        if (!explicit_shape && !o.autotune) tune_lookup(path, key, sh);
         if (o.autotune && nb > 0) {
-            const int cand_t[3] = {128, 256, 512};
-            const int cand_b[3] = {1, 2, 0};
-            double best = 1e30;
-            int bt = 256, bb = 0;
+            // coordinate search on the batch itself: the CTA shape first, then
+            // each of the ring stages, chunks per claim and early-stop
+            // granularity around the best so far (the persistent kernel alone
+            // is timed: the single-query kernels do not depend on the shape)
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            for (int ti = 0; ti < 3 && rc == BS_OK; ti++) {
-                for (int bi = 0; bi < 3 && rc == BS_OK; bi++) {
-                    if (shape(b, cand_t[ti], cand_b[bi]) != BS_OK) continue;
-                    if (launch_direct(b, nullptr) != BS_OK) { cudaGetLastError(); continue; }
-                    cudaEventRecord(e0, nullptr);
-                    for (int rep = 0; rep < 3; rep++) launch_direct(b, nullptr);
-                    cudaEventRecord(e1, nullptr);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = BS_ERR_CUDA; break; }
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    const double us = ms * 1000.0 / 3;
-                    if (us < best) { best = us; bt = cand_t[ti]; bb = cand_b[bi]; }
+            auto time_shape = [&](const Shape &c) -> double {
+                if (shape(b, c) != BS_OK) return 1e30;
+                if (launch_persistent(b, nullptr) != BS_OK) {
+                    cudaGetLastError();
+                    return 1e30;
                 }
+                cudaEventRecord(e0, nullptr);
+                for (int rep = 0; rep < 3; rep++) launch_persistent(b, nullptr);
+                cudaEventRecord(e1, nullptr);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = BS_ERR_CUDA;
+                    return 1e30;
+                }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                return ms * 1000.0 / 3;
+            };
+            Shape best_sh = sh;
+            double best = 1e30;
+            auto consider = [&](const Shape &c) {
+                if (rc != BS_OK) return;
+                const double us = time_shape(c);
+                if (us < best) {
+                    best = us;
+                    best_sh = c;
+                }
+            };
+            for (int t : {128, 256, 512})
+                for (int bp : {1, 2, 0}) consider(Shape{t, bp, kStages, 1, 0});
+            for (int st : {2, 4}) {
+                Shape c = best_sh;
+                c.stages = st;
+                consider(c);
+            }
+            for (int uc : {2, 4}) {
+                Shape c = best_sh;
+                c.unit_chunks = uc;
+                consider(c);
+            }
+            {
+                Shape c = best_sh;
+                c.stop_all = 1;
+                consider(c);
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
-            threads = bt;
-            bps = bb;
-            if (rc == BS_OK) tune_store(path, key, bt, bb, best);
+            sh = best_sh;
+            if (rc == BS_OK) tune_store(path, key, sh, best);
         }
-        if (rc == BS_OK) rc = shape(b, threads, bps);
+        if (rc == BS_OK) rc = shape(b, sh);
         if (rc == BS_OK) rc = capture(b);
     }
     cudaSetDevice(prev);
@@ -636,6 +726,20 @@ int bs_batch_info(const bs_batch *b, int32_t *threads, int32_t *ctas, int32_t *g
     if (threads) *threads = b->threads;
     if (ctas) *ctas = b->ctas;
     if (graph) *graph = b->graph_ok ? 1 : 0;
+    return BS_OK;
+}
+
+int bs_batch_get_shape(const bs_batch *b, bs_batch_shape *out) {
+    if (!b || !out) return BS_ERR_INVALID_ARG;
+    out->threads = b->threads;
+    out->blocks_per_sm = b->sh.bps;
+    out->ctas = b->ctas;
+    out->stages = b->sh.stages;
+    out->unit_chunks = b->sh.unit_chunks;
+    out->stop_rows = b->sh.stop_all ? 1024 : 256;
+    out->graph = b->graph_ok ? 1 : 0;
+    out->persistent_requests = b->k.nreq;
+    out->single_query_requests = (int32_t)b->plain.size();
     return BS_OK;
 }
 
@@ -783,6 +887,8 @@ int launch_slot(bs_server *S, Slot &sl, int nall, int nreq, uint32_t total_units
         k.nreq = nreq;
         k.total_units = total_units;
         k.total_segs = total_segs;
+        k.unit_chunks = 1;
+        k.total_claims = total_units;
         k.ctr = (uint32_t *)(sl.d_desc + sl.o_ctr);
         k.status = st;
         if (cudaMemcpyAsync(sl.d_desc, sl.h_desc, sl.o_ctr, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
@@ -798,7 +904,7 @@ int launch_slot(bs_server *S, Slot &sl, int nall, int nreq, uint32_t total_units
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, batch_kernel, k) != cudaSuccess) return BS_ERR_CUDA;
+        if (cudaLaunchKernelEx(&cfg, batch_fn(kStages), k) != cudaSuccess) return BS_ERR_CUDA;
     }
     // counts and the status word in one copy (the status word follows the counts)
     if (cudaMemcpyAsync(sl.h_desc + sl.o_counts, sl.d_desc + sl.o_counts, sl.o_status + 8 - sl.o_counts,
@@ -871,8 +977,9 @@ void dispatcher(bs_server *S) {
                 P.out = R.look.out_vals;
                 P.cap = q.bound;
                 P.count = R.look.count;
-                if (runs_plain(R)) {
+                if (S->o.single_query_kernels || runs_plain(R)) {
                     sl.plain.push_back(P);
+                    S->stats.single_query_queries++;
                 } else {
                     R.unit0 = units;
                     unit0[nk] = units;
@@ -882,6 +989,7 @@ void dispatcher(bs_server *S) {
                     seg0[nk] = segs;
                     segs += R.n_segs;
                     reqs[nk++] = R;
+                    S->stats.persistent_queries++;
                 }
                 sl.tickets.push_back(tk);
                 q.state = 1;
@@ -993,9 +1101,9 @@ int bs_server_create(const bs_server_opts *opts, bs_server **out) {
         // of different slots run side by side
         const size_t smem = smem_bytes(o.threads);
         int fit = 0;
-        if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(batch_fn(kStages), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel, o.threads, smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_fn(kStages), o.threads, smem) != cudaSuccess ||
             fit < 1) {
             cudaGetLastError();
             rc = BS_ERR_CUDA;

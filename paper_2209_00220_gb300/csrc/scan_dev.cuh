@@ -54,7 +54,8 @@ constexpr uint32_t kMsb = 0x80808080u;
 constexpr uint32_t kLow7 = 0x7F7F7F7Fu;
 constexpr int kScanThreads = 256;
 constexpr int kScanWarps = kScanThreads / 32;
-constexpr int kStages = 3;  // ring slots per warp in the batched kernel
+constexpr int kStages = 3;  // ring slots per warp in the batched kernel (default; 2..kStagesMax)
+constexpr int kStagesMax = 4;
 
 struct DLit {
     uint32_t len;      // bytes in the literal code
@@ -80,6 +81,9 @@ struct ScanK {
     uint64_t lo, hi;           // Bit-Packed: code range of the predicate
     int32_t invert;            // Bit-Packed: result = !(lo <= code <= hi)
     uint32_t fin_l, fin_e, fin_i;  // one literal: result = ((LT & fin_l) | (EQ & fin_e)) ^ (valid & fin_i), all-ones or zero each
+    uint32_t stop_all;         // early-stop granularity: 0 = a deeper level is read per 256-row group
+                               // (PP-VBS) or lane (ByteSlice) with pending rows, 1 = for the whole
+                               // 1024-row tile once any of its rows is pending
     const uint32_t *seed;
     uint32_t *out;
     uint32_t *status;
@@ -180,7 +184,7 @@ __device__ __forceinline__ void vbs_deeper(const ScanK &a, uint32_t t, uint32_t 
             mj = m2_pre;
         } else {
             const uint32_t bal = __ballot_sync(kFull, pend != 0u);
-            const uint32_t gact = (bal >> (lane & 24u)) & 0xFFu;
+            const uint32_t gact = a.stop_all ? bal : ((bal >> (lane & 24u)) & 0xFFu);
             mj = gact ? __ldg(a.mask[j] + wbase + lane) : 0u;
         }
         if (act1) {
@@ -253,7 +257,7 @@ __device__ __forceinline__ void bsl_deeper(const ScanK &a, uint32_t t, uint32_t 
     for (int j = 2; j <= a.K; j++) {
         const uint32_t pend = EQ1 | EQ2;
         if (!__any_sync(kFull, pend != 0u)) break;
-        if (pend) {
+        if (pend || a.stop_all) {
             uint32_t x[8];
             load_lane32(a.dense + (uint64_t)(j - 1) * a.slice_bytes + (uint64_t)t * kTileRows, lane, x);
             uint32_t lt, eq;

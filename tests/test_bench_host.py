@@ -76,3 +76,14 @@ def test_reference_arm_line():
     assert line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_oracle_sample_on_several_threads_agrees():
+    # the all-core oracle timing splits rows into ranges run by the oracle's
+    # own sequential code; the values found equal one sequential pass
+    values, lit = bench.make_column(1 << 18, 0)
+    rows = 200_003
+    _, m1, _, t1 = bench.oracle_sample(values, lit, rows, 1)
+    _, m4, _, t4 = bench.oracle_sample(values, lit, rows, 4)
+    assert t1 == 1 and t4 == 4
+    assert m1 == m4 == int((values[:rows] < lit).sum())

@@ -116,11 +116,20 @@ def test_batch_capacity_and_autotune(B, tmp_path):
     assert int(cnt.item()) == m
     assert np.array_equal(out[:50].cpu().numpy(), v[v < a][:50]) and np.all(out[50:].cpu().numpy() == -1)
     text = open(cache).read()
-    assert '"threads"' in text and '"blocks_per_sm"' in text
+    for key in ('"threads"', '"blocks_per_sm"', '"stages"', '"unit_chunks"', '"stop_rows"'):
+        assert key in text
+    sh = batch.shape()
+    assert sh["stages"] in (2, 3, 4) and sh["unit_chunks"] in (1, 2, 4) and sh["stop_rows"] in (256, 1024)
+    assert sh["persistent_requests"] == 1 and sh["single_query_requests"] == 0
     # a second batch with the same signature reuses the cached shape
     b2 = B.bs_batch_create([{"preds": [(col, "lt", a)], "out": out, "out_cap": 50, "count": cnt}],
                            tune_cache=cache)
-    assert b2.info()["threads"] == batch.info()["threads"]
+    sh2 = b2.shape()
+    for key in ("threads", "blocks_per_sm", "stages", "unit_chunks", "stop_rows"):
+        assert sh2[key] == sh[key], key
+    b2.launch()
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == m
     assert B.bs_last_device_error() == 0
 
 
@@ -165,4 +174,45 @@ def test_long_columns_take_single_query_kernels_in_batch_and_server(B):
         assert np.array_equal(srv.values(t, r["count"]).cpu().numpy(), w)
         srv.release(t)
     srv.destroy()
+    assert B.bs_last_device_error() == 0
+
+
+@pytest.mark.parametrize("shape", [{"stages": 2}, {"stages": 4}, {"unit_chunks": 2}, {"unit_chunks": 4},
+                                   {"stop_rows": 1024}, {"threads": 128, "blocks_per_sm": 1},
+                                   {"threads": 512, "stages": 4, "unit_chunks": 4, "stop_rows": 1024}])
+def test_every_tunable_shape_matches_oracle(B, shape):
+    """Each value the autotuner can pick for ring stages, chunks per claim and
+    early-stop granularity (and the CTA shapes), forced once: every request's
+    count, values and bit vector equal the oracle's."""
+    import torch
+    pool = _pool(B, seed=3)
+    rng = synth.u64(11, 2, 400)
+    ops = ("lt", "ge", "eq", "between", "ne")
+    reqs, expect = [], []
+    for i in range(24):
+        ci = int(rng[i] % np.uint64(len(pool) - 1))
+        v, col = pool[ci]
+        op = ops[i % len(ops)]
+        a, b = synth.pick_literals(v, op, float(10 ** (-3 + 2.5 * (int(rng[50 + i] % np.uint64(100)) / 100.0))), i)
+        mask = _mask(v, op, a, b)
+        n = v.size
+        out = torch.full((n + 1,), -7, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        bits = torch.zeros((n + 31) // 32, dtype=torch.int32, device="cuda")
+        reqs.append({"preds": [(col, op, a, b)], "out": out, "out_cap": n, "count": cnt, "bits": bits})
+        expect.append((mask, v))
+    batch = B.bs_batch_create(reqs, **shape)
+    got_shape = batch.shape()
+    for k, val in shape.items():
+        assert got_shape[k] == val, (k, got_shape)
+    batch.launch()
+    torch.cuda.synchronize()
+    for q, (mask, v) in zip(reqs, expect):
+        m = int(mask.sum())
+        assert int(q["count"].item()) == m
+        assert np.array_equal(q["out"][:m].cpu().numpy(), v[mask])
+        assert int(q["out"][m].item()) == -7 or m == q["out_cap"]
+        want = np.packbits(mask, bitorder="little")
+        want = np.concatenate([want, np.zeros((-want.size) % 4, np.uint8)]).view("<u4")
+        assert np.array_equal(q["bits"].cpu().numpy().view(np.uint32), want)
     assert B.bs_last_device_error() == 0

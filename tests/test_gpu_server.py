@@ -127,3 +127,28 @@ def test_server_reports_failed_launch_per_query(B):
     assert srv.stats()["failed"] == 1
     srv.destroy()
     assert B.bs_last_device_error() == 0
+
+
+def test_serial_single_query_server_matches_batched(B):
+    """Serial plain execution through the same dispatcher (one query per launch,
+    one slot, single-query kernels only) gives the batched server's results;
+    the per-path counters show which kernels served the queries."""
+    tables = [_table(B, 300007, 51), _table(B, 1 << 20, 61)]
+    qs = _queries(tables, 40, 9)
+    batched = B.bs_server_create(max_batch=16, slots=2, result_bytes=64 << 20, scratch_bytes=512 << 20)
+    serial = B.bs_server_create(max_batch=1, slots=1, result_bytes=64 << 20, scratch_bytes=512 << 20,
+                                single_query_kernels=True)
+    for srv in (batched, serial):
+        tickets = [srv.submit(p, pj) for p, pj, _ in qs]
+        for t, (p, pj, want) in zip(tickets, qs):
+            r = srv.wait(t, 60000)
+            assert r["status"] == 0 and r["count"] == want.size
+            assert np.array_equal(srv.values(t, r["count"]).cpu().numpy(), want)
+            srv.release(t)
+    sb, ss = batched.stats(), serial.stats()
+    assert sb["persistent_queries"] == len(qs) and sb["single_query_queries"] == 0
+    assert ss["single_query_queries"] == len(qs) and ss["persistent_queries"] == 0
+    assert ss["batches"] == len(qs) and ss["mean_batch"] == 1.0
+    batched.destroy()
+    serial.destroy()
+    assert B.bs_last_device_error() == 0

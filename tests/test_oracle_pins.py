@@ -396,3 +396,19 @@ def test_categorical_column_second_level_and_roundtrip():
     big = np.arange(70000, dtype=np.int32)
     ob = orc.OracleColumn(big, "ppvbs", categorical=True)
     assert ob.K == 3 and np.array_equal(ob.decode_values(), big)
+
+
+@pytest.mark.parametrize("n,d,s,mono,step", [(100003, 24, 0.7, True, 32 * 311), (50000, 12, 1.0, False, 777),
+                                             (4097, 16, 1.2, True, 1)])
+def test_vbs_range_decode_equals_one_pass(n, d, s, mono, step):
+    """The range decoder (cursors started where a full pass has them) gives
+    every row's value, for ranges that start at any row, including mid-word."""
+    v = synth.config_sweep_column(n, d, s, 5 + d, monotone=mono)
+    o = orc.OracleColumn(v, "ppvbs")
+    parts = [o.decode_values_range(a, min(a + step, n)) for a in range(0, n, step)] if step > 1 else \
+        [o.decode_values_range(a, a + 1) for a in range(0, n, 97)]
+    got = np.concatenate(parts)
+    if step > 1:
+        assert np.array_equal(got, v)
+    else:
+        assert np.array_equal(got, v[::97])
