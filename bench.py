@@ -9,9 +9,12 @@ and skew, Section 6.1), encoded as PP-VBS; the step scans it with `v < c`
 matching row to int32. Inputs (the encoded column, ~1.2 GB, larger than the
 129 MB L2) are resident in HBM before the timed region; no L2 flush is needed.
 
-Under torchrun (N > 1) every rank holds its own 2^30-row shard (rows are
-independent; no collective is on the data path) and the value is the rows of
-all ranks over the slowest rank's time (weak scaling).
+Under torchrun (N > 1) the ranks hold row shards of ONE column of N x 2^30 rows,
+each encoded against the whole column's dictionary (gathered once over a host
+group); the step's one exchange is an all-gather of the ranks' selected-row
+counts, whose prefix places each rank's values in the whole column's output
+order. The value is the rows of all ranks over the slowest rank's time (weak
+scaling).
 
 Beside the step, the line carries two more measurements (skip them with
 --no-batched / --no-serving):
@@ -189,6 +192,26 @@ def make_column(n, seed):
     values = synth.config_sweep_column(n, 12, 1.0, seed)
     lit, _ = synth.pick_literals(values, "lt", 0.10, seed)
     return values, lit
+
+
+def shard_column(n_per_rank, world, rank, group=None, seed=0):
+    """This rank's row range of ONE column of n_per_rank * world rows (the
+    bench column, generated piecewise: row i depends on i alone), the whole
+    column's dictionary and counts (all-gathered from the ranks over `group`),
+    and the literal (picked on rank 0's rows, shared by all ranks). With one
+    rank this is make_column's column and literal."""
+    from paper_2209_00220_gb300 import shard, synth
+    total = n_per_rank * world
+    lo, hi = shard.shard_range(total, world, rank)
+    values = synth.config_sweep_column(hi - lo, 12, 1.0, seed, start=lo)
+    dictionary = shard.global_dictionary(values, group)
+    lit = synth.pick_literals(values, "lt", 0.10, seed)[0] if rank == 0 else 0
+    if world > 1:
+        import torch.distributed as dist
+        box = [lit]
+        dist.broadcast_object_list(box, src=0, group=group)
+        lit = int(box[0])
+    return values, lo, hi, dictionary, int(lit)
 
 
 def oracle_sample(values, lit, rows, threads=1):
@@ -402,50 +425,10 @@ def poisson_arrivals(rate, count, seed):
     return np.cumsum(-np.log1p(-u) / rate)
 
 
-def serve_plain(B, queries, max_rows):
-    """Serial plain execution: per query bs_scan_conj, bs_lookup and the count
-    read back to the host. Returns per-query service seconds and counts."""
-    import torch
-    bits = torch.empty((max_rows + 31) // 32, dtype=torch.int32, device="cuda")
-    out = torch.empty(max_rows, dtype=torch.int32, device="cuda")
-    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-    big = max(queries, key=lambda q: q[2])[1]
-    work = torch.empty(B.bs_lookup_workspace_bytes(big) // 4 + 1, dtype=torch.int32, device="cuda")
-    stream = torch.cuda.current_stream()
-    h_cnt = torch.empty(1, dtype=torch.int64, pin_memory=True)
-
-    def one(q):
-        preds, proj, n = q
-        B.bs_scan_conj(preds, out=bits, stream=stream)
-        B.bs_lookup(proj, bits, out=out, count=cnt, workspace=work, stream=stream)
-        h_cnt.copy_(cnt, non_blocking=True)
-        stream.synchronize()
-        return int(h_cnt.item())
-
-    for q in queries[:8]:
-        one(q)
-    svc, counts = np.empty(len(queries)), np.empty(len(queries), dtype=np.int64)
-    for i, q in enumerate(queries):
-        t0 = time.perf_counter()
-        counts[i] = one(q)
-        svc[i] = time.perf_counter() - t0
-    return svc, counts, (bits, out, cnt, work)
-
-
-def queue_fifo(arrivals, svc):
-    """Completion times of a single FIFO server with the given service times."""
-    done = np.empty_like(arrivals)
-    t = 0.0
-    for i, (a, s) in enumerate(zip(arrivals, svc)):
-        t = max(t, a) + s
-        done[i] = t
-    return done
-
-
 def serve_at(B, srv, prepared, arrivals, want_counts):
     """Submits each query at its arrival time; a collector thread waits on the
     tickets in order, records the latency from the scheduled arrival and
-    releases the result."""
+    releases the result. Returns (latencies s, completion times s, bad)."""
     import queue
     import threading
     q = queue.Queue()
@@ -457,7 +440,7 @@ def serve_at(B, srv, prepared, arrivals, want_counts):
         for _ in range(len(prepared)):
             i, ticket, t_sub = q.get()
             r = srv.wait(ticket, 600000)
-            if r["status"] != 0 or r["count"] != want_counts[i]:
+            if r["status"] != 0 or (want_counts is not None and r["count"] != want_counts[i]):
                 bad.append(i)
             lat[i] = (t_sub - arrivals[i]) + r["latency_us"] * 1e-6
             done_t[i] = t_sub + r["latency_us"] * 1e-6  # seconds after the stream's start
@@ -476,57 +459,87 @@ def serve_at(B, srv, prepared, arrivals, want_counts):
     return lat, done_t, bad
 
 
+def _stream_stats(srv, prepared, arr, counts):
+    st0 = srv.stats()
+    lat, done_t, bad = serve_at(None, srv, prepared, arr, counts)
+    st1 = srv.stats()
+    m = len(prepared)
+    return {"served_qps": round(m / float(done_t.max()), 1),
+            "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+            "batches": int(st1["batches"] - st0["batches"]),
+            "mean_batch": round((st1["completed"] - st0["completed"]) / max(1, st1["batches"] - st0["batches"]), 2),
+            "persistent_queries": int(st1["persistent_queries"] - st0["persistent_queries"]),
+            "single_query_queries": int(st1["single_query_queries"] - st0["single_query_queries"]),
+            "ok": not bad}
+
+
 def run_serving(B, rates=(1000, 3000, 10000, 30000, 100000), seconds=2.0, max_queries=6000, distinct=1024, scale=1.0,
-                seed=0):
-    """The arrival stream draws (seeded, uniform) from `distinct` generated
-    queries; plain service times and counts are measured once per distinct query."""
+                seed=0, tables=None, label="resident PP-VBS columns of 2^28..2^30 rows"):
+    """Poisson streams of 1-3-predicate conjunction + lookup queries drawn
+    (seeded, uniform) from `distinct` generated queries, served twice through
+    the same dispatcher and admission: by the batching server (64 queries per
+    launch, 2 slots, continuous batching) and by serial plain execution (one
+    query per launch, one slot, the single-query kernels). Both are measured
+    live: latency from the scheduled arrival to the host seeing the result
+    complete. Offered rates: the listed ones and 0.5x, 0.8x and 0.95x the
+    batching server's measured capacity (its throughput at the highest rate),
+    so that p50 / p99 also describe a steady state below capacity. Every
+    count is checked against the serial plain result of the same query, and
+    a sample of values against plain bs_scan_conj + bs_lookup calls."""
     import torch
     from paper_2209_00220_gb300 import synth
     t_setup = time.time()
-    tables = serving_tables(B, seed, scale)
+    if tables is None:
+        tables = serving_tables(B, seed, scale)
     setup_s = time.time() - t_setup
     distinct_q = serving_queries(tables, distinct, seed)
     max_rows = max(t[0] for t in tables)
-    svc_d, counts_d, keep = serve_plain(B, distinct_q, max_rows)
     nq = max_queries
     pick = (synth.u64(seed, 5353, nq) % np.uint64(distinct)).astype(np.int64)
     queries = [distinct_q[i] for i in pick]
-    svc, counts = svc_d[pick], counts_d[pick]
-    del keep
     torch.cuda.empty_cache()
-    srv = B.bs_server_create(max_batch=64, slots=2, result_bytes=16 << 30, scratch_bytes=16 << 30)
+    budget = dict(result_bytes=16 << 30, scratch_bytes=16 << 30)
+    srv = B.bs_server_create(max_batch=64, slots=2, **budget)
+    plain = B.bs_server_create(max_batch=1, slots=1, single_query_kernels=True, **budget)
     prepared = [srv.prepare(p, proj) for p, proj, _ in queries]
-    # warm-up: the server's first batches
-    warm = [srv.submit(pq) for pq in prepared[:64]]
-    for t in warm:
-        srv.wait(t, 600000)
-        srv.release(t)
+    # the exact counts of every distinct query, from serial plain execution
+    counts_d = np.zeros(distinct, dtype=np.int64)
+    tickets = [plain.submit(srv.prepare(p, proj)) for p, proj, _ in distinct_q]
+    for i, t in enumerate(tickets):
+        r = plain.wait(t, 600000)
+        counts_d[i] = r["count"]
+        plain.release(t)
+    counts = counts_d[pick]
+    for s_ in (srv, plain):  # warm-up: the first batches
+        warm = [s_.submit(pq) for pq in prepared[:64]]
+        for t in warm:
+            s_.wait(t, 600000)
+            s_.release(t)
     old_si = sys.getswitchinterval()
     sys.setswitchinterval(2e-4)
     runs = []
     try:
-        for k, rate in enumerate(rates):
+        def one(rate, k, sub):
             m = int(min(nq, max(200, rate * seconds)))
             arr = poisson_arrivals(rate, m, seed + k)
-            st0 = srv.stats()
-            lat, done_t, bad = serve_at(B, srv, prepared[:m], arr, counts)
-            st1 = srv.stats()
-            span = float(done_t.max())
-            pdone = queue_fifo(arr, svc[:m])
-            plat = pdone - arr
-            runs.append({
-                "offered_qps": rate, "queries": m,
-                "served_qps": round(m / span, 1), "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
-                "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
-                "plain_qps": round(m / float(pdone.max()), 1),
-                "plain_p50_ms": round(1e3 * float(np.percentile(plat, 50)), 3),
-                "plain_p99_ms": round(1e3 * float(np.percentile(plat, 99)), 3),
-                "batches": int(st1["batches"] - st0["batches"]),
-                "mean_batch": round((st1["completed"] - st0["completed"]) / max(1, st1["batches"] - st0["batches"]), 2),
-                "identical_counts": not bad})
+            r = {"offered_qps": round(rate, 1), "queries": m}
+            if sub:
+                r["below_capacity"] = sub
+            b = _stream_stats(srv, prepared[:m], arr, counts)
+            p = _stream_stats(plain, prepared[:m], arr, counts)
+            r.update({k2: v for k2, v in b.items()})
+            r.update({"plain_" + k2: v for k2, v in p.items() if k2 in ("served_qps", "p50_ms", "p99_ms", "ok")})
+            return r
+
+        for k, rate in enumerate(sorted(rates)):
+            runs.append(one(rate, k, None))
+        capacity = max(r["served_qps"] for r in runs)
+        for k, f in enumerate((0.5, 0.8, 0.95)):
+            runs.append(one(f * capacity, 100 + k, f))
     finally:
         sys.setswitchinterval(old_si)
-    # exact results: a sample of queries' values, served vs plain
+    # exact results: a sample of queries' values, served vs plain calls
     same = True
     bits = torch.empty((max_rows + 31) // 32, dtype=torch.int32, device="cuda")
     for i in range(0, nq, max(1, nq // 24)):
@@ -541,14 +554,37 @@ def run_serving(B, rates=(1000, 3000, 10000, 30000, 100000), seconds=2.0, max_qu
         srv.release(t)
         same = same and int(c.item()) == r["count"] and torch.equal(v[: r["count"]], got)
     srv.destroy()
+    plain.destroy()
     rows_in_hbm = sum(4 * t[0] for t in tables)
-    return {"columns": 16, "tables": [{"rows": t[0], "cols": t[3]} for t in tables],
-            "resident_rows": int(rows_in_hbm), "setup_s": round(setup_s, 1),
-            "distinct_queries": distinct, "plain_capacity_qps": round(nq / float(svc.sum()), 1),
-            "plain_mean_service_ms": round(1e3 * float(svc.mean()), 4),
-            "runs": runs, "identical_values_sample": bool(same),
-            "latency": "scheduled Poisson arrival to completion; plain = FIFO queue over measured serial service times",
-            "server": {"max_batch": 64, "slots": 2, "result_bytes": 16 << 30, "scratch_bytes": 16 << 30}}
+    return {"workload": label, "columns": sum(len(t[1]) for t in tables),
+            "tables": [{"rows": t[0], "cols": t[3]} for t in tables],
+            "resident_rows": int(rows_in_hbm // 4), "setup_s": round(setup_s, 1), "distinct_queries": distinct,
+            "capacity_qps": capacity, "runs": runs, "identical_values_sample": bool(same),
+            "identical_counts": all(r["ok"] and r["plain_ok"] for r in runs),
+            "latency": "scheduled Poisson arrival to the host seeing the result complete, both servers live",
+            "server": {"max_batch": 64, "slots": 2, "result_bytes": 16 << 30, "scratch_bytes": 16 << 30},
+            "plain": {"max_batch": 1, "slots": 1, "single_query_kernels": True}}
+
+
+def small_serving_tables(B, seed=0):
+    """16 resident PP-VBS columns of 2^22..2^24 rows (4 tables of 4), short
+    enough that every query runs in the persistent kernel."""
+    from paper_2209_00220_gb300 import synth
+    r = synth.u64(seed, 5454, 32)
+    tables = []
+    for t, n in enumerate((1 << 22, 1 << 23, 11863283, 1 << 24)):
+        cols, samples, meta = [], [], []
+        for j in range(4):
+            i = 4 * t + j
+            d = 10 + int(r[i] % np.uint64(15))
+            s = float(r[16 + i] % np.uint64(1000)) / 1000 * 1.5
+            v = synth.config_sweep_column(n, d, s, 9000 + i)
+            idx = (synth.u64(i, 97, 1 << 16) % np.uint64(n)).astype(np.int64)
+            samples.append(v[idx])
+            cols.append(B.bs_encode_column(v, "ppvbs"))
+            meta.append((d, round(s, 3)))
+        tables.append((n, cols, samples, meta))
+    return tables
 
 
 def run_reference(args):
@@ -611,10 +647,22 @@ def run_ours(args):
     from paper_2209_00220_gb300 import bytestore as B
 
     n = args.rows
-    values, lit = make_column(n, rank)
-    t0 = time.time()
-    col = B.bs_encode_column(values, "ppvbs", device=local, keep_host=True)
-    encode_s = time.time() - t0
+    if ws > 1:
+        # row shards of one column: each rank holds a 2^30-row range, encoded
+        # against the whole column's dictionary (gathered over a host group)
+        from paper_2209_00220_gb300 import shard
+        host_group = dist.new_group(backend="gloo")
+        values, lo, hi, dictionary, lit = shard_column(n, ws, rank, host_group)
+        t0 = time.time()
+        col = shard.encode_shard(B, values, "ppvbs", dictionary, device=local, keep_host=True)
+        encode_s = time.time() - t0
+        n = hi - lo
+        counts_all = torch.zeros(ws, dtype=torch.int64, device="cuda")
+    else:
+        values, lit = make_column(n, rank)
+        t0 = time.time()
+        col = B.bs_encode_column(values, "ppvbs", device=local, keep_host=True)
+        encode_s = time.time() - t0
     info = col.info()
     nw = col.n_words
     bits = torch.empty(nw, dtype=torch.int32, device="cuda")
@@ -626,9 +674,13 @@ def run_ours(args):
     pred = [(col, "lt", lit)]
 
     # the step: the whole query in the fused kernel -- the predicate's result
-    # bit vector, the values of the selected rows and their count
+    # bit vector, the values of the selected rows and their count; with row
+    # shards, also the one exchange of the query path: every rank's count, whose
+    # exclusive prefix places its values in the whole column's output order
     def step():
         B.bs_scan_lookup(pred, out=out, count=count, bits=bits, workspace=fws, stream=stream)
+        if ws > 1:
+            dist.all_gather_into_tensor(counts_all, count)
 
     for _ in range(args.warmup):
         step()
@@ -737,7 +789,9 @@ def run_ours(args):
                    "rows_per_gpu": n, "selected": m, "selectivity": round(m / n, 5), "K": info["max_code_bytes"],
                    "step": "bs_scan_lookup: result bit vector + values + count in one kernel",
                    "l2": "inputs larger than L2 (BS_1 = %d MB), no flush" % (n >> 20),
-                   "parallelism": "row shards, replicas" if ws > 1 else "single GPU",
+                   "parallelism": ("row shards of one %d-row column (dictionary gathered from the ranks, "
+                                   "selected-row counts all-gathered for output offsets)" % (n * ws))
+                   if ws > 1 else "single GPU",
                    "host_numa_node": numa},
         "scan_grows_s": round(n / fused_s / 1e9, 3),
         "lookup_gvals_s": round(m / fused_s / 1e9, 3),
@@ -782,6 +836,10 @@ def run_ours(args):
     if not args.no_serving:
         torch.cuda.empty_cache()
         line["serving"] = run_serving(B, scale=args.serve_scale)
+        torch.cuda.empty_cache()
+        line["serving_short_columns"] = run_serving(
+            B, rates=(1000, 10000, 100000), max_queries=4000, tables=small_serving_tables(B),
+            label="resident PP-VBS columns of 2^22..2^24 rows (the persistent kernel serves every query)")
     if rank == 0 and ws == 1 and not args.no_cpu:
         cores = host_cores()
         rows = min(n, args.cpu_rows)

@@ -56,6 +56,8 @@ def _load():
             lib.synth_u64.restype = None
             lib.synth_zipf.argtypes = [u64, u64, u64, u64, dbl, vp, i32]
             lib.synth_zipf.restype = i32
+            lib.synth_zipf_at.argtypes = [u64, u64, u64, u64, u64, dbl, vp, i32]
+            lib.synth_zipf_at.restype = i32
             lib.synth_feistel.argtypes = [vp, u64, i32, u64, vp, i32]
             lib.synth_feistel.restype = i32
             lib.synth_gather.argtypes = [vp, u64, vp, vp, i32]
@@ -83,10 +85,11 @@ def u64(seed: int, stream: int, n: int, start: int = 0) -> np.ndarray:
     return out
 
 
-def zipf_ranks(n: int, N: int, s: float, seed: int, stream: int = 0) -> np.ndarray:
-    """n ranks in [0, N) with P(rank r) proportional to (r + 1)^-s."""
+def zipf_ranks(n: int, N: int, s: float, seed: int, stream: int = 0, start: int = 0) -> np.ndarray:
+    """n ranks in [0, N) with P(rank r) proportional to (r + 1)^-s: rows
+    start..start+n-1 of the stream (each row depends on its index alone)."""
     out = np.empty(n, dtype=np.uint32)
-    rc = _load().synth_zipf(seed, stream, n, N, float(s), _ptr(out), _threads())
+    rc = _load().synth_zipf_at(seed, stream, start, n, N, float(s), _ptr(out), _threads())
     if rc != 0:
         raise ValueError("synth_zipf failed (%d) for N=%d s=%g" % (rc, N, s))
     return out
@@ -162,10 +165,11 @@ def config_single_column(seed: int = 0, n: int = 1 << 20, distinct: int = 65536,
     return zipf_column(n, distinct, s, seed, mapping=table), domain
 
 
-def config_sweep_column(n: int, d: int, s: float, seed: int, monotone: bool = False) -> np.ndarray:
-    """Values in [0, 2^d) for d < 32 (whole int32 range for d = 32), rank ~ Zipf(s)."""
+def config_sweep_column(n: int, d: int, s: float, seed: int, monotone: bool = False, start: int = 0) -> np.ndarray:
+    """Values in [0, 2^d) for d < 32 (whole int32 range for d = 32), rank ~ Zipf(s);
+    rows start..start+n-1 of the column (a row range of a longer column)."""
     N = 1 << d
-    r = zipf_ranks(n, N, s, seed)
+    r = zipf_ranks(n, N, s, seed, start=start)
     if not monotone:
         r = feistel(r, d, seed ^ 0x5A5A)
     return r.view(np.int32)

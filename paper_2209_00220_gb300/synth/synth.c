@@ -91,6 +91,7 @@ void synth_u64(uint64_t seed, uint64_t stream, uint64_t start, uint64_t n, uint6
 
 typedef struct {
     uint64_t key, N;
+    uint64_t start;  /* out[i] is row start + i of the stream */
     double s;
     /* inverse-CDF path */
     const double *cdf;
@@ -119,7 +120,7 @@ static double zHinv(double u, double s) {
 static void zipf_uniform_range(void *p, uint64_t b, uint64_t e) {
     zipf_ctx *c = (zipf_ctx *)p;
     for (uint64_t i = b; i < e; i++) {
-        uint64_t z = draw(c->key, i);
+        uint64_t z = draw(c->key, c->start + i);
         /* high 64 bits of z * N: an index in [0, N) */
         unsigned __int128 m = (unsigned __int128)z * (unsigned __int128)c->N;
         c->out[i] = (uint32_t)(m >> 64);
@@ -129,7 +130,7 @@ static void zipf_uniform_range(void *p, uint64_t b, uint64_t e) {
 static void zipf_cdf_range(void *p, uint64_t b, uint64_t e) {
     zipf_ctx *c = (zipf_ctx *)p;
     for (uint64_t i = b; i < e; i++) {
-        double u = u01(draw(c->key, i));
+        double u = u01(draw(c->key, c->start + i));
         uint64_t g = (uint64_t)(u * (double)c->G);
         if (g >= c->G) g = c->G - 1;
         uint64_t r = c->guide[g];
@@ -144,7 +145,7 @@ static void zipf_rejinv_range(void *p, uint64_t b, uint64_t e) {
         for (uint64_t attempt = 0;; attempt++) {
             /* attempt t > 0 draws from its own derived stream */
             uint64_t key = attempt ? sm64_mix(c->key + attempt * 0xD1B54A32D192ED03ULL) : c->key;
-            double u01v = u01(draw(key, i));
+            double u01v = u01(draw(key, c->start + i));
             double u = c->h_hi + u01v * (c->h_lo - c->h_hi);
             double x = zHinv(u, c->s);
             double kf = floor(x + 0.5);
@@ -160,11 +161,15 @@ static void zipf_rejinv_range(void *p, uint64_t b, uint64_t e) {
 }
 
 /* Returns 0 on success, -1 on bad arguments, -2 on allocation failure. */
-int synth_zipf(uint64_t seed, uint64_t stream, uint64_t n, uint64_t N, double s, uint32_t *out, int nthreads) {
+/* Rows start .. start + n - 1 of the stream (row i depends on i alone, so a
+ * column can be generated in disjoint pieces). */
+int synth_zipf_at(uint64_t seed, uint64_t stream, uint64_t start, uint64_t n, uint64_t N, double s, uint32_t *out,
+                  int nthreads) {
     if (N == 0 || N > 4294967296ULL || s < 0.0) return -1;
     zipf_ctx c;
     memset(&c, 0, sizeof c);
     c.key = stream_key(seed, stream);
+    c.start = start;
     c.N = N;
     c.s = s;
     c.out = out;
@@ -196,6 +201,10 @@ int synth_zipf(uint64_t seed, uint64_t stream, uint64_t n, uint64_t N, double s,
     c.h_hi = zH((double)N + 0.5, s);
     parallel_range(zipf_rejinv_range, &c, n, nthreads);
     return 0;
+}
+
+int synth_zipf(uint64_t seed, uint64_t stream, uint64_t n, uint64_t N, double s, uint32_t *out, int nthreads) {
+    return synth_zipf_at(seed, stream, 0, n, N, s, out, nthreads);
 }
 
 /* --------------------------------------------------------------- Feistel */

@@ -152,3 +152,64 @@ def test_gpu_shards_concatenate_to_whole_column(B, layout):
         assert np.array_equal(np.concatenate(words), want_bits), (layout, op)
         assert np.array_equal(np.concatenate(vals), want_vals), (layout, op)
     assert B.bs_last_device_error() == 0
+
+
+def _bench_rank(rank, world, port, q):
+    try:
+        import sys
+        import torch.distributed as dist
+        os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        sys.path.insert(0, root)
+        import bench
+        from paper_2209_00220_gb300 import bytestore as B
+        n = 3 * 1024 + 100
+        values, lo, hi, d, lit = bench.shard_column(n, world, rank)
+        col = shard.encode_shard(B, values, "ppvbs", d, host_only=True)
+        codes, _ = B.bs_column_row_codes(col)
+        vals = orc.lookup(values, orc.scan_values(values, "lt", lit))
+        off, total = shard.output_offset(vals.size)
+        dist.barrier()
+        dist.destroy_process_group()
+        q.put((rank, lo, hi, lit, codes, off, total, vals))
+    except Exception as e:  # report to the parent instead of hanging it
+        q.put((rank, "error", repr(e)))
+
+
+def test_bench_row_shards_on_two_gloo_ranks(B):
+    """The multi-rank bench's setup on CPU ranks with host-only columns: the
+    ranks' row ranges are pieces of one column (the one-rank bench column
+    extended), their codes are the whole column's, the literal is shared,
+    and the values placed at the exchanged offsets are the whole column's."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    world = 2
+    ps = [ctx.Process(target=_bench_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in ps:
+        p.start()
+    got = [q.get(timeout=300) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+    errs = [g for g in got if g[1] == "error"]
+    assert not errs, errs
+    n = 3 * 1024 + 100
+    v = synth.config_sweep_column(n * world, 12, 1.0, 0)
+    one, _ = bench.make_column(n, 0)
+    assert np.array_equal(v[:n], one)  # the one-rank column is this column's first rows
+    whole = B.bs_encode_column(v, "ppvbs", host_only=True)
+    wc, _ = B.bs_column_row_codes(whole)
+    lits = {g[3] for g in got}
+    assert len(lits) == 1
+    lit = lits.pop()
+    want = orc.lookup(v, orc.scan_values(v, "lt", lit))
+    out = np.full(want.size, -1, np.int64)
+    for rank, lo, hi, _, codes, off, total, vals in sorted(got, key=lambda g: g[0]):
+        assert np.array_equal(codes, wc[lo:hi])
+        assert total == want.size
+        out[off:off + vals.size] = vals
+    assert np.array_equal(out, want.astype(np.int64))
