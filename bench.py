@@ -673,23 +673,46 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     pred = [(col, "lt", lit)]
 
-    # the step: the whole query in the fused kernel -- the predicate's result
-    # bit vector, the values of the selected rows and their count; with row
-    # shards, also the one exchange of the query path: every rank's count, whose
-    # exclusive prefix places its values in the whole column's output order
+    ubits = torch.empty_like(bits)
+    uout = torch.empty_like(out)
+    ucount = torch.zeros_like(count)
+    work = torch.empty(B.bs_lookup_workspace_bytes(col) // 4 + 1, dtype=torch.int32, device="cuda")
+
+    # the two implementations of the query: the paper's operators (scan
+    # kernel -> result bit vector -> lookup kernels: count, offsets, gather)
+    # and the fused kernel (bit vector, values and count in one launch). Each
+    # produces the bit vector, the values of the selected rows and their count.
+    def unfused(o=None, c=None):
+        B.bs_scan(col, "lt", lit, 0, out=ubits, stream=stream)
+        B.bs_lookup(col, ubits, out=uout if o is None else o, count=ucount if c is None else c, workspace=work,
+                    stream=stream)
+
+    def fused(o=None, c=None):
+        B.bs_scan_lookup(pred, out=out if o is None else o, count=count if c is None else c, bits=bits,
+                         workspace=fws, stream=stream)
+
+    run = unfused if args.step == "unfused" else fused
+    step_count = ucount if args.step == "unfused" else count
+
+    # the step: the query; with row shards also the one exchange of the query
+    # path: every rank's count, whose exclusive prefix places its values in the
+    # whole column's output order
     def step():
-        B.bs_scan_lookup(pred, out=out, count=count, bits=bits, workspace=fws, stream=stream)
+        run()
         if ws > 1:
-            dist.all_gather_into_tensor(counts_all, count)
+            dist.all_gather_into_tensor(counts_all, step_count)
 
     for _ in range(args.warmup):
-        step()
+        unfused()
+        fused()
     torch.cuda.synchronize()
     m = int(count.item())
     if m > out.numel():
         out = torch.empty(m, dtype=torch.int32, device="cuda")
+        uout = torch.empty(m, dtype=torch.int32, device="cuda")
         for _ in range(2):
-            step()
+            unfused()
+            fused()
         torch.cuda.synchronize()
 
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -710,36 +733,27 @@ def run_ours(args):
     if dist:
         dist.barrier()
     total_ms = start.elapsed_time(end)
-    fused_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     t = torch.tensor([total_ms], device="cuda")
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
-    h_bits = bits.cpu()
 
-    # the same query as the paper's operators: scan kernel -> bit vector ->
-    # lookup kernels (count, offsets, gather); its results must be identical
-    ubits = torch.empty_like(bits)
-    uout = torch.empty_like(out)
-    ucount = torch.zeros_like(count)
-    work = torch.empty(B.bs_lookup_workspace_bytes(col) // 4 + 1, dtype=torch.int32, device="cuda")
-    for _ in range(args.warmup):
-        B.bs_scan(col, "lt", lit, 0, out=ubits, stream=stream)
-        B.bs_lookup(col, ubits, out=uout, count=ucount, workspace=work, stream=stream)
+    # each kernel of both implementations timed alone (CUDA events, same stream)
     scan_ms = _timed(stream, lambda: B.bs_scan(col, "lt", lit, 0, out=ubits, stream=stream), args.steps)
     look_ms = _timed(stream, lambda: B.bs_lookup(col, ubits, out=uout, count=ucount, workspace=work,
                                                    stream=stream), args.steps)
-    same_as_unfused = int(ucount.item()) == m and bool(torch.equal(ubits, bits)) and \
+    fused_ms = _timed(stream, fused, args.steps)
+    same = int(ucount.item()) == m and int(count.item()) == m and bool(torch.equal(ubits, bits)) and \
         bool(torch.equal(uout[:m], out[:m]))
-    del ubits, uout, work
+    h_bits = bits.cpu()
 
     # end to end through the public API: every step's result (the count and the
     # whole value buffer, copied without a host round trip for the count) lands
     # in pinned host memory; two result buffers alternate so that one step's
-    # copy overlaps the next step's kernel
+    # copy overlaps the next step's kernels
     cap = out.numel()
-    outs = [out, torch.empty_like(out)]
-    cnts = [count, torch.zeros_like(count)]
+    outs = [out, uout] if args.step == "fused" else [uout, out]
+    cnts = [torch.zeros_like(count), torch.zeros_like(count)]
     h_outs = [torch.empty(cap, dtype=torch.int32, pin_memory=True) for _ in range(2)]
     h_cnts = [torch.empty(1, dtype=torch.int64, pin_memory=True) for _ in range(2)]
     copier = torch.cuda.Stream()
@@ -751,7 +765,7 @@ def run_ours(args):
         k = i % 2
         if freed[k] is not None:
             stream.wait_event(freed[k])  # buffer k's previous copy is done
-        B.bs_scan_lookup(pred, out=outs[k], count=cnts[k], bits=bits, workspace=fws, stream=stream)
+        run(outs[k], cnts[k])
         ready = torch.cuda.Event()
         ready.record(stream)
         copier.wait_event(ready)
@@ -770,7 +784,7 @@ def run_ours(args):
     samp = slice(0, 1 << 20)
     want = orc.scan_values(values[samp], "lt", lit)
     ok = bool(np.array_equal(h_bits[: want.size].numpy().view(np.uint32), want)) and \
-        int(h_cnt.item()) == int(np.count_nonzero(values < lit)) and e2e_ok and same_as_unfused
+        int(h_cnt.item()) == int(np.count_nonzero(values < lit)) and e2e_ok and same
 
     hbm, peak_kind = _peaks()
     hb = h_bits.numpy().view(np.uint32)
@@ -781,49 +795,51 @@ def run_ours(args):
     scan_s = float(np.mean(scan_ms)) / 1e3
     look_s = float(np.mean(look_ms)) / 1e3
     value = n * ws * args.steps / (total_ms / 1e3) / 1e9
+
+    def roof(name, byts, secs, traffic_name, kernel):
+        return {"bound": "hbm", "achieved": round(byts / secs / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(byts / secs / 1e9 / hbm, 4), "traffic": _scaled(profile_traffic(traffic_name), n),
+                "kernel": kernel, "peak_kind": peak_kind, "algorithmic_bytes": int(byts)}
+
+    r_scan = roof("scan", scan_bytes, scan_s, "scan_dense_ppvbs_sweep", "scan_dense_kernel<PP-VBS>")
+    r_look = roof("lookup", look_bytes, look_s, "lookup_ppvbs_k2_sweep",
+                  "bs_lookup: lookup_count + lookup_scan + lookup_gather<PP-VBS, K<=2>")
+    r_fused = roof("fused", fused_bytes, fused_s, "fused_ppvbs_k2_sweep", "fused_kernel<K<=2, v < c> (bs_scan_lookup)")
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "Grows/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": WORKLOAD,
                    "rows_per_gpu": n, "selected": m, "selectivity": round(m / n, 5), "K": info["max_code_bytes"],
-                   "step": "bs_scan_lookup: result bit vector + values + count in one kernel",
+                   "step": ("bs_scan + bs_lookup: scan kernel, then count, offsets and gather kernels"
+                            if args.step == "unfused" else
+                            "bs_scan_lookup: result bit vector + values + count in one kernel"),
                    "l2": "inputs larger than L2 (BS_1 = %d MB), no flush" % (n >> 20),
                    "parallelism": ("row shards of one %d-row column (dictionary gathered from the ranks, "
                                    "selected-row counts all-gathered for output offsets)" % (n * ws))
                    if ws > 1 else "single GPU",
                    "host_numa_node": numa},
-        "scan_grows_s": round(n / fused_s / 1e9, 3),
-        "lookup_gvals_s": round(m / fused_s / 1e9, 3),
-        # the fused kernel is the whole step
-        "roofline": {"bound": "hbm", "achieved": round(fused_bytes / fused_s / 1e9, 1), "peak": hbm,
-                     "unit": "GB/s", "frac": round(fused_bytes / fused_s / 1e9 / hbm, 4),
-                     "traffic": _scaled(profile_traffic("fused_ppvbs_k2_sweep"), n),
-                     "kernel": "fused_kernel<K<=2, v < c> (bs_scan_lookup)", "peak_kind": peak_kind,
-                     "algorithmic_bytes": int(fused_bytes)},
-        "unfused": {
-            "step_ms": round(float(np.median(scan_ms)) + float(np.median(look_ms)), 4),
-            "grows_s": round(n / (scan_s + look_s) / 1e9, 3),
-            "scan_ms": round(float(np.median(scan_ms)), 4), "lookup_ms": round(float(np.median(look_ms)), 4),
-            "lookup_gvals_s": round(m / look_s / 1e9, 3), "identical_to_fused": same_as_unfused,
-            "roofline_scan": {"bound": "hbm", "achieved": round(scan_bytes / scan_s / 1e9, 1), "peak": hbm,
-                              "unit": "GB/s", "frac": round(scan_bytes / scan_s / 1e9 / hbm, 4),
-                              "traffic": _scaled(profile_traffic("scan_dense_ppvbs_sweep"), n),
-                              "kernel": "scan_dense_kernel<PP-VBS>", "algorithmic_bytes": int(scan_bytes)},
-            "roofline_lookup": {"bound": "hbm", "achieved": round(look_bytes / look_s / 1e9, 1), "peak": hbm,
-                                "unit": "GB/s", "frac": round(look_bytes / look_s / 1e9 / hbm, 4),
-                                "traffic": _scaled(profile_traffic("lookup_ppvbs_k2_sweep"), n),
-                                "kernel": "bs_lookup: lookup_count + lookup_scan + lookup_gather<PP-VBS, K<=2>",
-                                "algorithmic_bytes": int(look_bytes)}},
+        "scan_grows_s": round(n / scan_s / 1e9, 3),
+        "scan_ms": round(float(np.median(scan_ms)), 4),
+        "lookup_gvals_s": round(m / look_s / 1e9, 3),
+        "lookup_ms": round(float(np.median(look_ms)), 4),
+        # the step's dominant kernel: the lookup (unfused step) or the fused kernel
+        "roofline": r_look if args.step == "unfused" else r_fused,
+        "roofline_scan": r_scan,
+        "fused": {"ms": round(float(np.median(fused_ms)), 4), "grows_s": round(n / fused_s / 1e9, 3),
+                  "lookup_gvals_s": round(m / fused_s / 1e9, 3), "identical_to_unfused": same,
+                  "roofline": r_fused},
+        "unfused": {"ms": round(float(np.median(scan_ms)) + float(np.median(look_ms)), 4),
+                    "grows_s": round(n / (scan_s + look_s) / 1e9, 3), "roofline_lookup": r_look},
         "e2e": {"value": round(n / e2e_s / 1e9, 4), "unit": "Grows/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 4 * cap + 8, "steps": e2e_steps,
                 "note": "count + value buffer to pinned host memory each step; copies overlap the next step"},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (4 if args.step == "unfused" else 1),
         "clocks": clocks.summary(),
         "encode_s": round(encode_s, 2),
         "parity_sample_ok": ok,
     }
-    del outs, h_outs, out
+    del outs, h_outs, out, uout, ubits, work
     torch.cuda.empty_cache()
     if not args.no_small:
         line["small"] = run_small_block(B)
@@ -1072,6 +1088,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--step", default="unfused", choices=["unfused", "fused"],
+                    help="the timed step: scan + lookup kernels (default) or the fused kernel")
     ap.add_argument("--rows", type=int, default=1 << 30)
     ap.add_argument("--ref-rows", type=int, default=1 << 24, help="oracle rows per step of --impl reference")
     ap.add_argument("--cpu-rows", type=int, default=1 << 28, help="oracle rows timed on all host cores")

@@ -237,7 +237,7 @@ int bs_lookup_codes(const bs_column *col, const uint32_t *d_bits, uint64_t *d_co
 /* ------------------------------------------------- fused scan + lookup */
 
 /* Device workspace bytes bs_scan_lookup needs for a projection column of this
- * length (8 bytes per 1024 rows plus 256). */
+ * length (8 bytes per 4096 rows plus 256). */
 uint64_t bs_scan_lookup_workspace_bytes(const bs_column *proj);
 
 /* Fused scan + lookup (Section 2.2's query shape: a conjunction of predicates

@@ -16,10 +16,20 @@
 //      value below, so a reader never sees a state without its value);
 //      then publishes its inclusive prefix;
 //   3. gathers the projected column's values of the selected rows of its
-//      tiles with the lookup's per-tile code (lookup_dev.cuh), while the next
-//      unit's tiles are already in flight into the ring.
+//      tiles with the lookup's per-tile code (lookup_dev.cuh).
 // Steps 2 and 3 of a unit come after step 1 of the warp's next unit (see the
-// main loop), so that look-backs rarely wait.
+// main loop), so that look-backs rarely wait. The ring and the gather's
+// scratch share a warp's shared memory (the next tiles are copied in after
+// the gather), which with at most 51 registers a thread keeps five CTAs (40
+// warps) of the specialised variant resident per SM. The gather reads a tile's BS_1 bytes again, a unit
+// or two after the scan copied them: the scan's copies ask L2 to keep those
+// lines (evict_last) and the gather's reads let them go (evict_first), so the
+// second read is an L2 hit rather than a second trip to DRAM.
+// Measured and dropped (2^30 rows, v < c at 13.7 %): one tile per unit with
+// the tile held in shared memory from scan to gather (no second read, but a
+// look-back per tile: with ~5,000 warps claiming, the walk to the nearest
+// published prefix outgrew its 128-descriptor window: 1.67 ms); units of 8
+// or 16 tiles (1.31 / 2.20 ms: the second read of BS_1 misses L2 more).
 // Because units are claimed in order, every unit a look-back waits for has
 // been claimed by a running warp, so the wait always ends; it is bounded
 // anyway (a timeout is recorded in the status word and the warp goes on).
@@ -151,11 +161,12 @@ __device__ __forceinline__ void gather_any_tile(const LookK &a, uint64_t t, uint
     }
 }
 
-// Shared memory: per warp the ring's two slices, then the gather's scratch;
-// after the warps, the values of the 256 one-byte PP-VBS codes.
+// Shared memory: per warp the ring's two slices, sharing their bytes with the
+// gather's scratch; after the warps, the values of the 256 one-byte PP-VBS
+// codes.
 template <int KMAX>
 struct FuseSmem {
-    static constexpr size_t warp = 2 * kTileRows + sizeof(WarpSmemT<KMAX>);
+    static constexpr size_t warp = sizeof(WarpSmemT<KMAX>) > 2 * kTileRows ? sizeof(WarpSmemT<KMAX>) : 2 * kTileRows;
     static constexpr size_t total = kFuseWarps * warp + 256 * sizeof(int32_t);
 };
 
@@ -163,13 +174,13 @@ struct FuseSmem {
 // itself, SPEC = (HI0 << 2) | (HI1 << 1) | NEED_EQ as in the scan kernel;
 // SPEC < 0: any predicates and projection (run-time dispatch).
 template <int KMAX, int SPEC>
-__global__ void __launch_bounds__(kFuseThreads) fused_kernel(const FuseK f) {
+__global__ void __launch_bounds__(kFuseThreads, SPEC >= 0 ? 5 : 4) fused_kernel(const FuseK f) {
     extern __shared__ __align__(16) unsigned char fsm[];
     constexpr bool kSpec = SPEC >= 0;
     constexpr bool HI0 = (SPEC & 4) != 0, HI1 = (SPEC & 2) != 0, NEED_EQ = (SPEC & 1) != 0;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint8_t *ring = fsm + warp * FuseSmem<KMAX>::warp;
-    WarpSmemT<KMAX> &sm = *reinterpret_cast<WarpSmemT<KMAX> *>(ring + 2 * kTileRows);
+    WarpSmemT<KMAX> &sm = *reinterpret_cast<WarpSmemT<KMAX> *>(ring);
     int32_t *val1 = reinterpret_cast<int32_t *>(fsm + kFuseWarps * FuseSmem<KMAX>::warp);
     const LookK &L = f.look;
     if (L.layout == BS_PPVBS && threadIdx.x < 256) val1[threadIdx.x] = __ldg(f.val1 + threadIdx.x);
@@ -181,12 +192,16 @@ __global__ void __launch_bounds__(kFuseThreads) fused_kernel(const FuseK f) {
     const uint32_t rbase = (uint32_t)__cvta_generic_to_shared(ring);
     const uint32_t n_tiles = L.n_tiles;
     const uint64_t n = L.n;
+    uint64_t pol_keep;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol_keep));
     auto issue = [&](uint32_t t, int stage) {
         if (ring_on && t < n_tiles) {
             const uint8_t *g = slice + (uint64_t)t * kTileRows;
             const uint32_t s = rbase + (uint32_t)stage * kTileRows;
-            cp_async16(s + lane * 16u, g + lane * 16u);
-            cp_async16(s + 512u + lane * 16u, g + 512u + lane * 16u);
+            asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(s + lane * 16u),
+                         "l"(g + lane * 16u), "l"(pol_keep) : "memory");
+            asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(s + 512u + lane * 16u),
+                         "l"(g + 512u + lane * 16u), "l"(pol_keep) : "memory");
         }
         cp_async_commit();  // one group per slot, empty or not
     };
@@ -269,7 +284,6 @@ __global__ void __launch_bounds__(kFuseThreads) fused_kernel(const FuseK f) {
         }
         uint64_t base = unit_offset(f, cur, tot_c, lane);
         const uint32_t nn = claim(f.ticket, lane);
-        start_unit(nn);  // its tiles fly while `cur` is gathered
         const uint32_t t0 = cur * kFuseTiles;
 #pragma unroll
         for (int i = 0; i < kFuseTiles; i++) {
@@ -279,6 +293,8 @@ __global__ void __launch_bounds__(kFuseThreads) fused_kernel(const FuseK f) {
             }
             base += tc_c[i];
         }
+        __syncwarp();
+        start_unit(nn);  // the ring shares the gather's shared memory: refilled after the gather
         cur = nxt;
         tot_c = tot_n;
 #pragma unroll
@@ -287,192 +303,6 @@ __global__ void __launch_bounds__(kFuseThreads) fused_kernel(const FuseK f) {
             tc_c[i] = tc_n[i];
         }
         nxt = nn;
-    }
-    cp_async_wait<0>();
-}
-
-// ---------------------------------------------------------------------------
-// The query whose projection is its single predicate's own PP-VBS column with
-// codes of at most two bytes (the bench's query). One unit is one tile, so a
-// tile's BS_1 bytes and M_2 words, copied once into a ring slot for the
-// predicate, are still there when its values are decoded: the column's bytes
-// are read from memory once. A warp's ring has three slots: the tile being
-// decoded (scanned one step earlier), the tile being scanned and the tile in
-// flight. Per step: scan the next tile and publish its count; look back for
-// the current tile's offset; decode the current tile's selected rows -- their
-// first byte from the ring slot (tile-permuted order), their second byte from
-// the tile's BS_2 segment staged in shared memory, the value from the one- or
-// two-byte table -- and store them coalesced.
-struct __align__(16) Vbs2Warp {
-    uint8_t slot[3][kTileRows + kTileWords * 4];  // BS_1 (tile order) then M_2 words
-    uint32_t seg[kTileRows / 4 + 4];               // the tile's BS_2 segment
-    uint16_t list[kTileRows];                      // selected rows of the tile, ascending
-    uint32_t pref[kTileWords];                     // per lane word: its first BS_2 byte in seg
-};
-constexpr uint32_t kVbs2Slot = kTileRows + kTileWords * 4;
-constexpr size_t kVbs2Smem = kFuseWarps * sizeof(Vbs2Warp) + 256 * sizeof(int32_t);
-static_assert(sizeof(Vbs2Warp) % 16 == 0 && kVbs2Slot % 16 == 0, "ring slots take 16-byte copies");
-
-// Values of the selected rows of tile t (sel: the lane's result word, m2: its
-// M_2 word; goff / seg_lo / seg_hi: the lane's group offset into BS_2 and the
-// tile's BS_2 byte range) at output slots base.. (coalesced).
-__device__ __forceinline__ void vbs2_decode(const LookK &a, uint64_t t, const uint8_t *slot, uint32_t sel, uint32_t m2,
-                                            uint32_t goff, uint32_t seg_lo, uint32_t seg_hi, uint64_t base,
-                                            Vbs2Warp &w, const int32_t *val1, uint32_t lane) {
-    const uint32_t cnt = __popc(sel);
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t v = __shfl_up_sync(kFull, incl, d);
-        if (lane >= (uint32_t)d) incl += v;
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    const uint32_t c2 = __popc(m2);
-    uint32_t inc2 = c2;
-#pragma unroll
-    for (int d = 1; d < 8; d <<= 1) {
-        const uint32_t v = __shfl_up_sync(kFull, inc2, d);
-        if ((lane & 7u) >= (uint32_t)d) inc2 += v;
-    }
-    // the tile's BS_2 bytes, four words per lane in flight
-    const bool has2 = a.K >= 2;
-    if (has2) {
-        const uint32_t w0 = seg_lo >> 2, w1 = (seg_hi + 3) >> 2;
-        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(a.deep[2]);
-        constexpr uint32_t kSegWords = sizeof(w.seg) / 4;
-        const uint32_t nseg = min(w1 - w0, kSegWords);
-        for (uint32_t i0 = 0; i0 < nseg; i0 += 32u * kUnroll) {
-            uint32_t r[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; u++) {
-                const uint32_t i = i0 + (uint32_t)u * 32u + lane;
-                r[u] = i < nseg ? __ldg(s32 + w0 + i) : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; u++) {
-                const uint32_t i = i0 + (uint32_t)u * 32u + lane;
-                if (i < nseg) w.seg[i] = r[u];
-            }
-        }
-    }
-    w.pref[lane] = goff + inc2 - c2 - seg_lo;
-    uint32_t pos = incl - cnt, r = sel;
-    while (r) {
-        const uint32_t b = __ffs(r) - 1;
-        r &= r - 1;
-        w.list[pos++] = (uint16_t)(lane * 32u + b);
-    }
-    __syncwarp();
-    const uint8_t *seg = reinterpret_cast<const uint8_t *>(w.seg) + (seg_lo & 3u);
-    const uint32_t *mw2 = reinterpret_cast<const uint32_t *>(slot + kTileRows);
-    const uint64_t room = a.out_cap > base ? a.out_cap - base : 0;
-    const uint32_t lim = (uint32_t)(room < total ? room : total);
-    int32_t *dst = a.out_vals + base;
-    auto value_of = [&](uint32_t i) -> int32_t {
-        const uint32_t q = w.list[i], wq = q >> 5, b = q & 31u;
-        const uint32_t mw = has2 ? mw2[wq] : 0u;  // no M_2 copied for one-byte columns
-        const uint32_t c1 = slot[tile_pos(q)];
-        const uint32_t c2b = seg[w.pref[wq] + __popc(mw & ((1u << b) - 1u))];
-        const uint32_t cc = ((mw >> b) & 1u) ? c2b : 0u;  // 0: a one-byte code
-        return cc ? __ldg(a.val2 + ((c1 << 8) | cc)) : val1[c1];
-    };
-    uint32_t i0 = 0;
-    for (; i0 + 32u * kUnroll <= lim; i0 += 32u * kUnroll) {
-        int32_t v[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; u++) v[u] = value_of(i0 + (uint32_t)u * 32u + lane);
-#pragma unroll
-        for (int u = 0; u < kUnroll; u++) dst[i0 + (uint32_t)u * 32u + lane] = v[u];
-    }
-    for (uint32_t i = i0 + lane; i < lim; i += 32u) dst[i] = value_of(i);
-    __syncwarp();  // the slot, list and segment are free again
-}
-
-template <bool HI0, bool HI1, bool NEED_EQ>
-__global__ void __launch_bounds__(kFuseThreads) fused_vbs2_kernel(const FuseK f) {
-    extern __shared__ __align__(16) unsigned char fsm[];
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    Vbs2Warp &W = reinterpret_cast<Vbs2Warp *>(fsm)[warp];
-    int32_t *val1 = reinterpret_cast<int32_t *>(fsm + kFuseWarps * sizeof(Vbs2Warp));
-    const LookK &L = f.look;
-    if (threadIdx.x < 256) val1[threadIdx.x] = __ldg(f.val1 + threadIdx.x);
-    __syncthreads();
-    const ScanK &A = f.pred[0].a;
-    const uint32_t n_tiles = L.n_tiles;
-    const uint64_t n = L.n;
-    const bool has2 = L.K >= 2;
-    const uint32_t rbase = (uint32_t)__cvta_generic_to_shared(&W.slot[0][0]);
-    auto issue = [&](uint32_t t, int s) {
-        if (t < n_tiles) {
-            const uint8_t *g = A.dense + (uint64_t)t * kTileRows;
-            const uint32_t sa = rbase + (uint32_t)s * kVbs2Slot;
-            cp_async16(sa + lane * 16u, g + lane * 16u);
-            cp_async16(sa + 512u + lane * 16u, g + 512u + lane * 16u);
-            if (has2) cp_async4(sa + kTileRows + lane * 4u, L.mask[2] + (uint64_t)t * kTileWords + lane);
-        }
-        cp_async_commit();  // one group per slot, empty or not
-    };
-    const uint32_t c0 = lit_byte(A.lit[0], 1);
-    const uint32_t add0 = thr_add(c0), add1 = thr_add(c0 + 1);
-    // the predicate on tile t from ring slot s (its count published), and the
-    // tile's BS_2 offsets for the decode one step later
-    struct Tile {
-        uint32_t sel, m2, goff, lo, hi, tc;
-    };
-    auto scan_step = [&](uint32_t t, int s) -> Tile {
-        Tile r{0, 0, 0, 0, 0, 0};
-        const uint8_t *slot = &W.slot[s][0];
-        const uint4 *sp = reinterpret_cast<const uint4 *>(slot);
-        const uint4 v0 = sp[lane], v1 = sp[32 + lane];
-        const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-        r.m2 = has2 ? reinterpret_cast<const uint32_t *>(slot + kTileRows)[lane] : 0u;
-        const uint64_t w = (uint64_t)t * kTileWords + lane;
-        const uint32_t sd = valid_mask(w * 32u, n);
-        r.sel = scan_tile<true, 1, HI0, HI1, NEED_EQ, true>(A, t, lane, x, sd, add0, add1, r.m2);
-        if (f.bits && w * 32u < n) st_stream(f.bits + w, r.sel);
-        r.tc = warp_sum(__popc(r.sel));
-        if (lane == 0) st_relaxed(f.desc + t, (t == 0 ? kDescInc : kDescAgg) | r.tc);
-        if (has2 && r.tc) {
-            const uint64_t e = (uint64_t)t * kGroupsPerTile;
-            r.goff = __ldg(L.off[2] + e + (lane >> 3));
-            r.lo = __ldg(L.off[2] + e);
-            r.hi = __ldg(L.off[2] + e + kGroupsPerTile);
-        }
-        return r;
-    };
-    // slots rotate: cur (decoded this step), nxt (scanned this step), pf (in
-    // flight). A tile is claimed only after the warp's look-back of the step,
-    // so that nothing between a tile's claim and the publication of its count
-    // waits for another warp: then every look-back wait is bounded by one
-    // decode and one scan of another warp, and no chain of waits forms.
-    int s_cur = 0, s_nxt = 1, s_pf = 2;
-    uint32_t cur = claim(f.ticket, lane);
-    issue(cur, s_cur);
-    uint32_t nxt = claim(f.ticket, lane);
-    issue(nxt, s_nxt);
-    Tile tc_cur{0, 0, 0, 0, 0, 0};
-    cp_async_wait<1>();
-    __syncwarp();
-    if (cur < n_tiles) tc_cur = scan_step(cur, s_cur);
-    while (cur < n_tiles) {
-        cp_async_wait<0>();  // nxt's slot has landed
-        __syncwarp();        // every lane's copies are visible to all lanes
-        Tile tc_nxt{0, 0, 0, 0, 0, 0};
-        if (nxt < n_tiles) tc_nxt = scan_step(nxt, s_nxt);
-        const uint64_t base = unit_offset(f, cur, tc_cur.tc, lane);
-        const uint32_t nn = claim(f.ticket, lane);
-        issue(nn, s_pf);  // flies while cur is decoded
-        if (tc_cur.tc && base < L.out_cap)
-            vbs2_decode(L, cur, &W.slot[s_cur][0], tc_cur.sel, tc_cur.m2, tc_cur.goff, tc_cur.lo, tc_cur.hi, base,
-                        W, val1, lane);
-        __syncwarp();  // slot cur is refilled two steps from now
-        const int s_free = s_cur;
-        s_cur = s_nxt;
-        s_nxt = s_pf;
-        s_pf = s_free;
-        cur = nxt;
-        nxt = nn;
-        tc_cur = tc_nxt;
     }
     cp_async_wait<0>();
 }
@@ -499,21 +329,10 @@ struct FusePick {
     size_t smem;
 };
 
-template <bool HI0, bool HI1>
-FuseFn pick_vbs2(bool need_eq) {
-    return need_eq ? fused_vbs2_kernel<HI0, HI1, true> : fused_vbs2_kernel<HI0, HI1, false>;
-}
-
-// spec >= 0 with kmax 2: the one-pass kernel (one tile per unit); spec >= 0
-// with kmax 4: the specialised four-tile kernel; otherwise the generic one.
+// spec >= 0 (kmax 2 or 4): the variant specialised for one literal on the
+// projection column; otherwise the generic one.
 FusePick pick_kernel(int kmax, int spec) {
-    if (kmax == 2 && spec >= 0) {
-        const bool eq = (spec & 1) != 0;
-        FuseFn fn = (spec & 4) ? pick_vbs2<true, true>(eq) : ((spec & 2) ? pick_vbs2<false, true>(eq)
-                                                                          : pick_vbs2<false, false>(eq));
-        return {fn, kVbs2Smem};
-    }
-    if (kmax == 2) return {fused_kernel<2, -1>, FuseSmem<2>::total};
+    if (kmax == 2) return {spec >= 0 ? pick_spec<2>(spec) : fused_kernel<2, -1>, FuseSmem<2>::total};
     if (kmax == 4) return {spec >= 0 ? pick_spec<4>(spec) : fused_kernel<4, -1>, FuseSmem<4>::total};
     return {fused_kernel<8, -1>, FuseSmem<8>::total};
 }
@@ -536,7 +355,8 @@ int prepare(const FusePick &k, int dev) {
 }  // namespace
 
 uint64_t scan_lookup_workspace_bytes(const Column &c) {
-    return kFuseWsHead + (uint64_t)c.n_tiles * 8;  // one descriptor per tile (the one-pass kernel's unit)
+    const uint64_t units = ((uint64_t)c.n_tiles + kFuseTiles - 1) / kFuseTiles;
+    return kFuseWsHead + units * 8;
 }
 
 int launch_scan_lookup(const Column *const *cols, const KPred *kp, int npred, const Column &proj, uint32_t *d_bits,
@@ -576,7 +396,6 @@ int launch_scan_lookup(const Column *const *cols, const KPred *kp, int npred, co
         spec = (pl.hi0 ? 4 : 0) | (pl.hi1 ? 2 : 0) | (pl.eq1 ? 1 : 0);
     if (spec == 4 || spec == 5) spec = -1;
     const FusePick k = pick_kernel(kmax, spec);
-    if (kmax == 2 && spec >= 0) f.n_units = proj.n_tiles;  // one tile per unit
     int rc = prepare(k, dev);
     if (rc) return rc;
     if (cudaMemsetAsync(d_ws, 0, scan_lookup_workspace_bytes(proj), s) != cudaSuccess) return BS_ERR_CUDA;

@@ -347,7 +347,15 @@ __device__ __forceinline__ void gather_dense_k2(const LookK &a, uint64_t t, uint
                                                 const int32_t *val1, uint32_t lane) {
     // one round of independent loads: BS_1, M_2 and (below) the BS_2 segment
     const uint4 *src = reinterpret_cast<const uint4 *>(a.dense + t * kTileRows);
-    const uint4 v0 = __ldg(src + lane), v1 = __ldg(src + 32 + lane);
+    uint4 v0, v1;
+    {
+        uint64_t pol;
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+        asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=r"(v0.x), "=r"(v0.y), "=r"(v0.z), "=r"(v0.w) : "l"(src + lane), "l"(pol));
+        asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=r"(v1.x), "=r"(v1.y), "=r"(v1.z), "=r"(v1.w) : "l"(src + 32 + lane), "l"(pol));
+    }
     const bool has2 = a.K >= 2;
     const uint32_t m2 = has2 ? __ldg(a.mask[2] + t * kTileWords + lane) : 0u;
     // ALU while they fly: output positions of this lane's rows
