@@ -358,7 +358,7 @@ def run_batched(B, warmup=2, steps=5, seed=0):
             "p50_ms": round(tb, 4), "p99_ms": round(tb, 4),
             "plain_p50_ms": round(float(np.percentile(lp, 50)), 4), "plain_p99_ms": round(float(np.percentile(lp, 99)), 4),
             "latency": "closed loop: all 256 submitted at t=0; a batched request completes with its launch",
-            "identical": same, "shape": batch.info(), "gpu_launches_per_batch": 2}
+            "identical": same, "shape": batch.shape(), "gpu_launches_per_batch": 2}
 
 
 # ------------------------------------------------------------ serving form
