@@ -16,7 +16,7 @@ import bench  # noqa: E402
 
 def test_committed_profiles_match_their_sources():
     # every summary the bench reads names its kernel sources and their hash
-    for name in ("scan_dense_ppvbs_sweep", "lookup_ppvbs_k2_sweep"):
+    for name in ("scan_dense_ppvbs_sweep", "lookup_ppvbs_k2_sweep", "fused_ppvbs_k2_sweep"):
         path = os.path.join(ROOT, "profiles", name + ".md")
         fields = {}
         with open(path) as f:
