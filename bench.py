@@ -843,6 +843,9 @@ def run_ours(args):
     torch.cuda.empty_cache()
     if not args.no_small:
         line["small"] = run_small_block(B)
+    if not args.no_sweep_slice:
+        torch.cuda.empty_cache()
+        line["sweep_d12"] = run_sweep_slice(B, n)
     if not args.no_batched:
         torch.cuda.empty_cache()
         line["batched"] = run_batched(B)
@@ -1022,16 +1025,15 @@ SWEEP_OPS = ("lt", "eq", "between")
 SWEEP_TARGETS = (0.001, 0.01, 0.1, 0.5, 0.9)
 
 
-def run_sweep(args):
-    """Every point of the single-column layout sweep (code widths x value
-    distributions x layouts x predicates x target selectivities) on one column
-    length: scan and lookup times, scan bytes and roofline fraction, one JSON
-    line per point, then one summary line per layout. Scan bytes replay every
-    16th tile (bs_scan_bytes_sampled) to bound the host time."""
+def sweep_points(B, n, widths, skews, hbm, emit=None):
+    """Points of the single-column layout sweep on one column length: for each
+    code width x value distribution, the column in every layout (fixed-width
+    layouts with the declared 2^d range), every predicate and target
+    selectivity; scan and lookup each timed alone (CUDA events, median of 5),
+    scan bytes from every 16th tile of the host replay (bs_scan_bytes_sampled).
+    Returns the points; emit(point) is called for each as it is measured."""
     import torch
-    from paper_2209_00220_gb300 import bytestore as B, synth
-    hbm, _ = _peaks()
-    n = args.rows
+    from paper_2209_00220_gb300 import synth
     stream = torch.cuda.current_stream()
     bits = torch.empty((n + 31) // 32, dtype=torch.int32, device="cuda")
     out = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -1049,9 +1051,9 @@ def run_sweep(args):
             ts.append(e0.elapsed_time(e1))
         return float(np.median(ts))
 
-    summary = {}
-    for d in SWEEP_WIDTHS:
-        for s in SWEEP_SKEWS:
+    points = []
+    for d in widths:
+        for s in skews:
             v = synth.config_sweep_column(n, d, s, d * 10 + int(s * 2))
             for lay in ("bitpacked", "byteslice", "ppvbs"):
                 opts = {} if lay == "ppvbs" else {"domain_bits": d, "domain_min": synth.domain_min_for_bits(d)}
@@ -1065,21 +1067,57 @@ def run_sweep(args):
                                                            stream=stream))
                         m = int(cnt.item())
                         by = B.bs_scan_bytes(col, op, a, b, stride=16)["bytes"]
-                        frac = by / (t_scan / 1e3) / 1e9 / hbm
-                        print(json.dumps({"d": d, "s": s, "layout": lay, "op": op, "target": tgt,
-                                          "selectivity": round(m / n, 5), "scan_ms": round(t_scan, 4),
-                                          "scan_frac": round(frac, 4), "scan_bytes_per_row": round(by / n, 4),
-                                          "lookup_ms": round(t_look, 4)}), flush=True)
-                        summary.setdefault(lay, []).append((frac, t_scan, t_look))
+                        pt = {"d": d, "s": s, "layout": lay, "op": op, "target": tgt,
+                              "selectivity": round(m / n, 5), "scan_ms": round(t_scan, 4),
+                              "scan_frac": round(by / (t_scan / 1e3) / 1e9 / hbm, 4),
+                              "scan_bytes_per_row": round(by / n, 4), "lookup_ms": round(t_look, 4)}
+                        points.append(pt)
+                        if emit:
+                            emit(pt)
                 del col, ws
-    for lay, pts in summary.items():
-        f = np.array([p[0] for p in pts])
-        print(json.dumps({"summary": lay, "points": len(pts), "scan_frac_mean": round(float(f.mean()), 4),
-                          "scan_frac_median": round(float(np.median(f)), 4),
-                          "scan_frac_p10": round(float(np.percentile(f, 10)), 4),
-                          "scan_ms_total": round(float(sum(p[1] for p in pts)), 2),
-                          "lookup_ms_total": round(float(sum(p[2] for p in pts)), 2), "rows": n}), flush=True)
+            del v
+    return points
+
+
+def sweep_summary(points, n):
+    out = {}
+    for lay in ("ppvbs", "byteslice", "bitpacked"):
+        pts = [p for p in points if p["layout"] == lay]
+        if not pts:
+            continue
+        f = np.array([p["scan_frac"] for p in pts])
+        out[lay] = {"points": len(pts), "scan_frac_mean": round(float(f.mean()), 4),
+                    "scan_frac_median": round(float(np.median(f)), 4),
+                    "scan_frac_p10": round(float(np.percentile(f, 10)), 4),
+                    "scan_ms_total": round(float(sum(p["scan_ms"] for p in pts)), 2),
+                    "lookup_ms_total": round(float(sum(p["lookup_ms"] for p in pts)), 2), "rows": n}
+        for op in SWEEP_OPS:
+            fo = [p["scan_frac"] for p in pts if p["op"] == op]
+            if fo:
+                out[lay]["scan_frac_mean_" + op] = round(float(np.mean(fo)), 4)
+    return out
+
+
+def run_sweep(args):
+    """--sweep: every point of the layout sweep (every width and distribution),
+    one JSON line per point, then one summary line per layout."""
+    from paper_2209_00220_gb300 import bytestore as B
+    hbm, _ = _peaks()
+    pts = sweep_points(B, args.rows, SWEEP_WIDTHS, SWEEP_SKEWS, hbm, emit=lambda p: print(json.dumps(p), flush=True))
+    for lay, sm in sweep_summary(pts, args.rows).items():
+        print(json.dumps(dict(summary=lay, **sm)), flush=True)
     return 0
+
+
+def run_sweep_slice(B, n):
+    """The sweep's d = 12, Zipf 1.0 column (Section 6.1's defaults) in the
+    default line: 3 layouts x {<, =, BETWEEN} x 5 target selectivities."""
+    hbm, _ = _peaks()
+    pts = sweep_points(B, n, (12,), (1.0,), hbm)
+    return {"workload": "layout sweep at d = 12, Zipf s = 1.0, %d rows" % n, "summary": sweep_summary(pts, n),
+            "points": [[p["layout"], p["op"], p["target"], p["selectivity"], p["scan_ms"], p["scan_frac"],
+                        p["lookup_ms"]] for p in pts],
+            "point_fields": ["layout", "op", "target", "selectivity", "scan_ms", "scan_frac", "lookup_ms"]}
 
 
 def main():
@@ -1096,6 +1134,7 @@ def main():
     ap.add_argument("--cpu-rows-single", type=int, default=1 << 26, help="oracle rows timed on one core")
     ap.add_argument("--no-small", action="store_true", help="skip the 2^20-row single-column block")
     ap.add_argument("--no-wide", action="store_true", help="skip the wide-table block")
+    ap.add_argument("--no-sweep-slice", action="store_true", help="skip the d = 12 slice of the layout sweep")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-request batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
