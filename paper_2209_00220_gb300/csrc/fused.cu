@@ -21,10 +21,11 @@
 // main loop), so that look-backs rarely wait. The ring and the gather's
 // scratch share a warp's shared memory (the next tiles are copied in after
 // the gather), which with at most 51 registers a thread keeps five CTAs (40
-// warps) of the specialised variant resident per SM. The gather reads a tile's BS_1 bytes again, a unit
-// or two after the scan copied them: the scan's copies ask L2 to keep those
-// lines (evict_last) and the gather's reads let them go (evict_first), so the
-// second read is an L2 hit rather than a second trip to DRAM.
+// warps) of the specialised variant resident per SM. The gather reads a
+// tile's BS_1 bytes again, a unit or two after the scan copied them: the
+// scan's copies ask L2 to keep those lines (evict_last) and the gather's reads
+// let them go (evict_first), so the second read is mostly an L2 hit rather
+// than a second trip to DRAM.
 // Measured and dropped (2^30 rows, v < c at 13.7 %): one tile per unit with
 // the tile held in shared memory from scan to gather (no second read, but a
 // look-back per tile: with ~5,000 warps claiming, the walk to the nearest

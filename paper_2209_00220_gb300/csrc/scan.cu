@@ -146,25 +146,26 @@ KernelFn pick_dense(bool hi0, bool hi1, bool need_eq) {
     }
 }
 
-// BETWEEN: both literals' first-byte thresholds as compile-time constants
-template <bool VBS, bool PF, bool HI0, bool HI1>
+// BETWEEN: both literals' first-byte thresholds as compile-time constants,
+// and whether the lower literal's byte-1 EQ mask is formed at all (EQ). The
+// high bit of c + 1 is set whenever that of c is, so (true, false) never
+// occurs for either pair.
+template <bool VBS, bool PF, bool HI0, bool HI1, bool EQ>
 KernelFn pick_between_hi(bool hi2, bool hi3) {
-    switch ((hi2 ? 2 : 0) | (hi3 ? 1 : 0)) {
-    case 0: return scan_dense_kernel<VBS, 2, HI0, HI1, true, PF, 0>;
-    case 1: return scan_dense_kernel<VBS, 2, HI0, HI1, true, PF, 1>;
-    case 2: return scan_dense_kernel<VBS, 2, HI0, HI1, true, PF, 2>;
-    default: return scan_dense_kernel<VBS, 2, HI0, HI1, true, PF, 3>;
-    }
+    if (hi2) return scan_dense_kernel<VBS, 2, HI0, HI1, EQ, PF, 3>;
+    return hi3 ? scan_dense_kernel<VBS, 2, HI0, HI1, EQ, PF, 1> : scan_dense_kernel<VBS, 2, HI0, HI1, EQ, PF, 0>;
+}
+
+template <bool VBS, bool PF, bool EQ>
+KernelFn pick_between_eq(bool hi0, bool hi1, bool hi2, bool hi3) {
+    if (hi0) return pick_between_hi<VBS, PF, true, true, EQ>(hi2, hi3);
+    return hi1 ? pick_between_hi<VBS, PF, false, true, EQ>(hi2, hi3)
+               : pick_between_hi<VBS, PF, false, false, EQ>(hi2, hi3);
 }
 
 template <bool VBS, bool PF>
-KernelFn pick_between(bool hi0, bool hi1, bool hi2, bool hi3) {
-    switch ((hi0 ? 2 : 0) | (hi1 ? 1 : 0)) {
-    case 0: return pick_between_hi<VBS, PF, false, false>(hi2, hi3);
-    case 1: return pick_between_hi<VBS, PF, false, true>(hi2, hi3);
-    case 2: return pick_between_hi<VBS, PF, true, false>(hi2, hi3);
-    default: return pick_between_hi<VBS, PF, true, true>(hi2, hi3);
-    }
+KernelFn pick_between(bool hi0, bool hi1, bool eq1, bool hi2, bool hi3) {
+    return eq1 ? pick_between_eq<VBS, PF, true>(hi0, hi1, hi2, hi3) : pick_between_eq<VBS, PF, false>(hi0, hi1, hi2, hi3);
 }
 
 template <int... Ks>
@@ -204,13 +205,13 @@ int launch_scan(const Column &c, const KPred &p, const uint32_t *d_seed, uint32_
     KernelFn fn;
     if (plan.vbs) {
         if (plan.pf)
-            fn = plan.nlit == 2 ? pick_between<true, true>(plan.hi0, plan.hi1, plan.hi2, plan.hi3)
+            fn = plan.nlit == 2 ? pick_between<true, true>(plan.hi0, plan.hi1, plan.eq1, plan.hi2, plan.hi3)
                                 : pick_dense<true, 1, true>(plan.hi0, plan.hi1, plan.eq1);
         else
-            fn = plan.nlit == 2 ? pick_between<true, false>(plan.hi0, plan.hi1, plan.hi2, plan.hi3)
+            fn = plan.nlit == 2 ? pick_between<true, false>(plan.hi0, plan.hi1, plan.eq1, plan.hi2, plan.hi3)
                                 : pick_dense<true, 1, false>(plan.hi0, plan.hi1, plan.eq1);
     } else {
-        fn = plan.nlit == 2 ? pick_between<false, false>(plan.hi0, plan.hi1, plan.hi2, plan.hi3)
+        fn = plan.nlit == 2 ? pick_between<false, false>(plan.hi0, plan.hi1, plan.eq1, plan.hi2, plan.hi3)
                             : pick_dense<false, 1, false>(plan.hi0, plan.hi1, plan.eq1);
     }
     fn<<<grid_for(fn, c.n_tiles, dev), kScanThreads, 0, s>>>(a);

@@ -444,7 +444,9 @@ inline void plan_scan(const Column &c, const KPred &p, const uint32_t *d_seed, b
     a.lit[1].jend = nlit == 2 ? std::min((int)l1.len + 1, K) : 1;  // BETWEEN's upper end: v <= c2
     // the EQ mask of byte 1 matters if a deeper level can still decide
     // "smaller", or if the predicate reads it directly
-    plan.eq1 = need_eq0 || l0.len >= 2 || nlit == 2;
+    // (BETWEEN: the lower end needs it only when its literal has a second
+    // byte; rows equal to a one-byte lower literal are settled, not smaller)
+    plan.eq1 = need_eq0 || l0.len >= 2;
     if (c.layout == BS_PPVBS) {
         for (int j = 2; j <= c.K; j++) {
             a.mask[j] = c.d_mask[j];
@@ -463,7 +465,7 @@ inline void plan_scan(const Column &c, const KPred &p, const uint32_t *d_seed, b
     // common enough that most tiles have some (more than one per tile on
     // average; 2^30-row columns of 12 to 20 bits: 3-9 % faster `<` and `=`
     // scans than a threshold of four per tile, BETWEEN unchanged)
-    if (allow_pf && c.layout == BS_PPVBS && c.K >= 2 && plan.eq1 && !d_seed) {
+    if (allow_pf && c.layout == BS_PPVBS && c.K >= 2 && (plan.eq1 || nlit == 2) && !d_seed) {
         if (c.first_byte_rows.size() == 256) {
             const uint32_t b1 = (uint32_t)(a.lit[1].left >> 56);
             const uint64_t share = c.first_byte_rows[cb] + (nlit == 2 && b1 != cb ? c.first_byte_rows[b1] : 0);
