@@ -114,8 +114,8 @@ def test_dense_dictionary_lookup_matches_oracle(B, name, values, dense, K):
 
 
 def test_dense_dictionary_projection_of_other_column(B):
-    """A conjunction over one column projected onto a dense-dictionary column:
-    the arithmetic decode reads the projected column's own tables."""
+    """A predicate on one column projected onto a dense-dictionary column:
+    the values come from the projected column's own decode tables."""
     import torch
     n = 300007
     pv = _run(synth.config_sweep_column(n, 12, 1.0, 74), -77)
