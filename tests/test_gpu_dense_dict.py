@@ -1,15 +1,20 @@
-"""GPU parity of the lookup on PP-VBS columns whose dictionary is a run of
-consecutive integers, the shape of many real columns (ids, day numbers,
-small counters).
+"""GPU parity of the lookup on columns whose dictionary is a run of
+consecutive integers, the shape of many real columns (ids, day numbers, small
+counters, any domain whose every value occurs).
 
 Algorithm 1 gives the values of one leaf consecutive codes 1, 2, ... after
-their first byte, in dictionary order; on such columns a neighbouring value
-differs from its code's neighbour by one, so a decode that is off by one code
-(a wrong BS_2 rank, a wrong leaf) shows up here as a value off by one. Each
+their first byte, in dictionary order, and the lookup decodes a code of three
+or more bytes as dictionary entry leaf2[first two bytes] + rest - 1. On a
+dictionary of consecutive integers that entry is the run's first value plus
+the index, so the lookup computes it instead of reading it (as it does for
+ByteSlice and Bit-Packed codes, which index the sorted dictionary directly),
+and a decode that is off by one code shows up as a value off by one. Each
 case takes a Zipf column, maps its distinct values onto a run of consecutive
-integers (or onto a run with one hole), and compares bs_lookup and
-bs_scan_lookup with the oracle's decode at several predicates and
-selectivities, including runs that end at the int32 limits."""
+integers (or onto a run with one hole, which must read the dictionary), and
+compares bs_lookup and bs_scan_lookup with the oracle's decode at several
+predicates and selectivities, for codes of two to five bytes and runs that
+end at the int32 limits; the ByteSlice and Bit-Packed cases do the same for
+dictionary-coded columns."""
 import numpy as np
 import pytest
 
@@ -62,8 +67,24 @@ def _cases():
     yield "d10_uniform", _run(uni, -5), True, 2
     yield "d12_zipf1_one_gap", _run(z1, 0, gap_at=nd1 // 2), False, 2
     yield "d12_zipf1_gap_first", _run(z1, 0, gap_at=1), False, 2
-    # a run of consecutive integers with codes of up to four bytes: the table path
     yield "d12_monotone_k4", _run(mono, -5), True, 4
+    # codes of three to five bytes: the value of a long code is entry
+    # leaf2[first two bytes] + rest - 1 of the dictionary, which for a run of
+    # consecutive integers is that run's first value plus the index
+    u16 = synth.config_sweep_column(n, 16, 0.0, 81)
+    z16 = synth.config_sweep_column(n, 16, 1.0, 82)
+    z20 = synth.config_sweep_column(n, 20, 0.5, 83)
+    u24 = synth.config_sweep_column(n, 24, 0.0, 84)
+    m24 = synth.config_sweep_column(n, 24, 0.7, 85, monotone=True)
+    m20 = synth.config_sweep_column(n, 20, 1.0, 86, monotone=True)
+    nd24 = np.unique(u24).size
+    yield "d16_uniform_k3", _run(u16, 0), True, 3
+    yield "d16_zipf1_k3_one_gap", _run(z16, -40, gap_at=777), False, 3
+    yield "d20_zipf05_k4", _run(z20, -300), True, 4
+    yield "d24_uniform_k4_to_int32_max", _run(u24, INT32_MAX - nd24 + 1), True, 4
+    yield "d24_uniform_k4_one_gap", _run(u24, 5, gap_at=nd24 - 2), False, 4
+    yield "monotone_d24_k5_from_int32_min", _run(m24, INT32_MIN), True, 5
+    yield "monotone_d20_k5_one_gap", _run(m20, 0, gap_at=1000), False, 5
 
 
 CASES = list(_cases())
@@ -136,4 +157,37 @@ def test_dense_dictionary_projection_of_other_column(B):
     got, cnt = B.bs_lookup(proj, bits, out=out)
     assert int(cnt.item()) == want.size
     assert np.array_equal(got[: want.size].cpu().numpy(), want)
+    assert B.bs_last_device_error() == 0
+
+
+@pytest.mark.parametrize("layout", ["byteslice", "bitpacked"])
+def test_dense_dictionary_fixed_width_layouts(B, layout):
+    """Dictionary-coded ByteSlice and Bit-Packed columns (no declared domain:
+    the code is the value's index in the sorted dictionary)."""
+    import torch
+    n = (1 << 20) + 999
+    z = synth.config_sweep_column(n, 12, 1.0, 87)
+    u = synth.config_sweep_column(n, 20, 0.0, 88)
+    cases = (("d12_run", _run(z, -9)), ("d12_one_gap", _run(z, -9, gap_at=100)),
+             ("d20_run_to_int32_max", _run(u, INT32_MAX - np.unique(u).size + 1)),
+             ("d20_run_from_int32_min", _run(u, INT32_MIN)))
+    out = torch.full((n + 64,), -7, dtype=torch.int32, device="cuda")
+    for name, values in cases:
+        col = B.bs_encode_column(values, layout)
+        assert col.info()["n_dict"] == np.unique(values).size, name
+        dec = orc.OracleColumn(values, layout).decode_values()
+        assert np.array_equal(dec, values), name
+        for op, a, b in _checks(values):
+            want = orc.lookup(values, orc.scan_values(values, op, a, b))
+            bits = B.bs_scan(col, op, a, b)
+            got, cnt = B.bs_lookup(col, bits, out=out)
+            assert int(cnt.item()) == want.size, (name, op, a, b)
+            g = got.cpu().numpy()
+            assert np.array_equal(g[: want.size], want), (name, op, a, b)
+            assert np.all(g[want.size:] == -7), (name, op, a, b)
+            out.fill_(-7)
+            got, cnt = B.bs_scan_lookup([(col, op, a, b)], out=out)
+            assert int(cnt.item()) == want.size, (name, "fused", op, a, b)
+            assert np.array_equal(got[: want.size].cpu().numpy(), want), (name, "fused", op, a, b)
+            out.fill_(-7)
     assert B.bs_last_device_error() == 0
