@@ -75,3 +75,34 @@ def test_noalloc_lookup_long_and_short_columns_alternating(B):
         assert torch.equal(got[:m], want[:m]), k
         assert np.array_equal(got[:m].cpu().numpy(), v[v < lit]), k
     assert B.bs_last_device_error() == 0
+
+
+def test_noalloc_lookup_leaves_free_device_memory_unchanged(B):
+    """The point of the entry point: a caller running under a fixed device
+    memory budget (or in a section where no allocator may be touched) can
+    look up without the device's free memory moving. After one warm-up call
+    (the first call looks up the scratch array's address and loads the
+    kernels), a call on a new bit vector must leave cudaMemGetInfo's free
+    bytes exactly where they were, and still match bs_lookup."""
+    import torch
+    n = 9 * 16384 + 101
+    v = synth.config_sweep_column(n, 16, 0.5, 46)
+    col = B.bs_encode_column(v, "ppvbs")
+    lit0, _ = synth.pick_literals(v, "lt", 0.2, 1)
+    lit1, _ = synth.pick_literals(v, "ge", 0.4, 2)
+    bits0 = B.bs_scan(col, "lt", lit0)
+    bits1 = B.bs_scan(col, "ge", lit1)
+    want, want_cnt = B.bs_lookup(col, bits1)
+    out = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    B.bs_lookup_noalloc(col, bits0, out=out, count=cnt)  # warm-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    B.bs_lookup_noalloc(col, bits1, out=out, count=cnt)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
+    m = int(want_cnt.item())
+    assert int(cnt.item()) == m
+    assert torch.equal(out[:m], want[:m])
+    assert B.bs_last_device_error() == 0
